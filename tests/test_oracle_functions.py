@@ -1,0 +1,281 @@
+"""Pins for the oracle's function formulas (Sec. 3-6 of the paper).
+
+Hand-worked values at points where the formula collapses to a closed form,
+the exact optimum f(x^opt) = f_opt (General Setup), the Modified Schwefel
+residual at its printed optimum, composition limits (Eq. weight), invariances
+(rotation, separability), and brute-force grid minima on D = 2.
+"""
+import math
+
+import mpmath as mp
+import numpy as np
+import pytest
+
+from paper_1407_7737_gb300 import inputs
+
+FOPT = 100.0
+TWO20 = 2.0 ** -20
+
+
+def schwefel_residual():
+    """418.9829 - g1(420.9687462275036) to 40 digits (Eq. schwefel at z = 0)."""
+    mp.mp.dps = 40
+    w = mp.mpf("420.9687462275036")
+    return float(mp.mpf("418.9829") - w * mp.sin(mp.sqrt(w)))
+
+
+RES = schwefel_residual()
+
+
+# ---------------------------------------------------------------------------
+# basic functions on hand-picked z (scale, rotation and offset already applied)
+# ---------------------------------------------------------------------------
+def A7(w):  # one Schaffer F7 term
+    return (1 + math.sin(50 * w ** 0.2) ** 2) * math.sqrt(w)
+
+
+def g3(v):
+    return v * v / 4000 - math.cos(v) + 1
+
+
+HAND = [
+    ("sphere", [3, 4], 25.0),
+    ("ellipsoid", [3, 4], 1 * 9 + 2 * 16),
+    ("ellipsoid", [1, 1, 1], 6.0),
+    ("elliptic", [3, 4], 9 + 1e6 * 16),
+    ("elliptic", [1, 1, 1], 1 + 1e3 + 1e6),
+    ("discus", [3, 4], 9e6 + 16),
+    ("cigar", [3, 4], 9 + 16e6),
+    ("powers", [2, 2], math.sqrt(4 + 64)),
+    ("powers", [1, -1, 2], math.sqrt(1 + 1 + 64)),
+    ("sharpv", [3, 3, 4], 9 + 100 * 5),
+    ("step", [0.4, -0.6, 1.5, -1.49], 0 + 1 + 4 + 1),
+    ("weierstrass", [0.5, 0.25], 3 * (2 - TWO20)),
+    ("weierstrass", [0.0, 0.0, 0.0], 0.0),
+    ("griewank", [0.0, 0.0], 0.0),
+    ("griewank", [math.pi, 0.0], math.pi ** 2 / 4000 + 2),
+    ("griewank", [0.0, math.pi * math.sqrt(2)], 2 * math.pi ** 2 / 4000 + 2),
+    ("rastrigin", [0.5, 0.0], 20.25),
+    ("rastrigin", [1.0, 2.0], 5.0),
+    ("schafferf7", [0.0, 0.0, 0.0], 0.0),
+    ("schafferf7", [3.0, 4.0], (A7(5.0)) ** 2),
+    ("schafferf7", [3.0, 4.0, 0.0], (0.5 * (A7(5.0) + A7(4.0))) ** 2),
+    ("egr", [1.0, 1.0, 1.0], 0.0),
+    ("egr", [0.0, 0.0], 2 * g3(1.0)),
+    ("egr", [1.0, 0.0], g3(100.0) + g3(101.0)),
+    ("rosenbrock", [1.0, 1.0, 1.0], 0.0),
+    ("rosenbrock", [2.0, 3.0], 101.0),
+    ("rosenbrock", [0.0, 1.0, 2.0], 201.0),
+    ("schwefel", [400.0 - 420.9687462275036], 418.9829 - 400 * math.sin(20)),
+    ("schwefel", [600.0 - 420.9687462275036], 418.9829 - (400 * math.sin(20) - 1)),
+    ("schwefel", [-600.0 - 420.9687462275036], 418.9829 + 400 * math.sin(20) + 1),
+    ("schwefel", [0.0, 0.0], 2 * RES),
+    ("katsuura", [0.0, 0.0], 0.0),
+    ("katsuura", [0.5, 1.0], 0.0),
+    # 2 * 0.25 = 0.5 is half-way: the j = 1 term is 0.5 / 2, the rest vanish
+    ("katsuura", [0.5, 0.25], 2.5 * 1.5 ** (10 / 2 ** 1.2) - 2.5),
+    ("katsuura", [1.0 / 3.0], 10 * (1 + (1 - 2.0 ** -32) / 3) ** 10 - 10),
+    ("katsuura", [1.0 / 3.0, 0.0],
+     2.5 * (1 + (1 - 2.0 ** -32) / 3) ** (10 / 2 ** 1.2) - 2.5),
+    ("lunacek", [2.5, 2.5], 0.0),
+    ("lunacek", [-2.5, -2.5], 2.0),
+    ("lunacek", [3.0, 2.5], 20.25),
+    ("ackley", [1.0, 1.0], 20 - 20 * math.exp(-0.2)),
+    ("happycat", [-1.0, -1.0], 0.0),
+    ("happycat", [0.0, 0.0], 2 ** 0.25 + 0.5),
+    ("happycat", [1.0, 1.0], 2.0),
+    ("hgbat", [-1.0, -1.0], 0.0),
+    ("hgbat", [1.0, 0.0], 1.25),
+    ("hgbat", [2.0, 0.0], math.sqrt(12) + 2.5),
+    ("schafferf6", [0.0, 0.0], 0.0),
+    ("schafferf6", [math.pi, 0.0], 2 * (0.5 - 0.5 / (1 + 0.001 * math.pi ** 2) ** 2)),
+    ("schafferf6", [math.pi / 2, 0.0], 2 * (0.5 + 0.5 / (1 + 0.001 * math.pi ** 2 / 4) ** 2)),
+]
+
+
+@pytest.mark.parametrize("kind,z,expect", HAND)
+def test_basic_function_hand_values(orc, kind, z, expect):
+    got = orc.G(kind, z)
+    assert abs(got - expect) <= 1e-9 * max(1.0, abs(expect)), (kind, z, got, expect)
+
+
+def test_ackley_zero(orc):
+    assert abs(orc.G("ackley", [0.0, 0.0, 0.0])) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# instance-level pins
+# ---------------------------------------------------------------------------
+SCHWEFEL_MEMBERS = {15: None, 16: None}
+
+
+def expected_at_optimum(orc, fid, D, comp):
+    """F(x^{opt,comp}) from the paper: f_opt + bias_comp + lambda_comp G(o),
+    where G(o) = 0 except the Modified Schwefel residual per variable."""
+    if fid in (15, 16):
+        return FOPT + D * RES
+    if 23 <= fid <= 28:
+        sizes, _ = orc.layout(fid, D)
+        schw = {23: [0], 27: [3], 28: [3]}.get(fid, [])
+        return FOPT + sum(sizes[i] for i in schw) * RES
+    if fid < 23:
+        return FOPT
+    bias = [0, 100, 200, 300, 400][comp]
+    lam_schw = {  # lambda of each Schwefel member (Sec. 6)
+        30: {0: 1.0}, 31: {0: 0.25}, 32: {0: 2.5e-2}, 33: {2: 2.5}, 34: {2: 2.5},
+    }.get(fid, {})
+    g = lam_schw.get(comp, 0.0) * D * RES
+    if fid in (35, 36):
+        member = {35: [23, 24, 25], 36: [26, 27, 28]}[fid][comp]
+        g = expected_at_optimum(orc, member, D, 0) - FOPT
+    return FOPT + bias + g
+
+
+@pytest.mark.parametrize("D", [10, 31, 100])
+def test_value_at_optimum(orc, D):
+    for fid in range(37):
+        comps = orc.generate(fid, D, 0)
+        for c in range(len(comps)):
+            f = orc.evaluate(fid, D, 0, comps[c].o[None, :])[0]
+            exp = expected_at_optimum(orc, fid, D, c)
+            assert abs(f - exp) <= 1e-10 * abs(exp), (fid, c, f, exp)
+
+
+def test_sphere_is_rotation_invariant(orc):
+    for D in (10, 30, 100):
+        o = orc.generate(0, D, 3)[0].o
+        x = inputs.uniform(50, D, 1)
+        f = orc.evaluate(0, D, 3, x)
+        exp = ((x - o[None, :]) ** 2).sum(1) + FOPT
+        assert np.abs(f - exp).max() <= 1e-12 * exp.max()
+
+
+def test_rotated_with_identity_equals_unrotated(orc):
+    """ID 11 with R = I and S = identity is ID 10; ID 16 likewise is ID 15."""
+    D = 12
+    x = inputs.uniform(40, D, 2)
+    for rot_fid, plain_fid in ((11, 10), (16, 15)):
+        c = orc.generate(rot_fid, D, 4)[0]
+        c.S = np.arange(D, dtype=np.int32)
+        c.R = [np.eye(n) for n in c.blocks]
+        p = orc.generate(plain_fid, D, 4)[0]
+        p.o = c.o.copy()
+        a = orc.evaluate_given(rot_fid, D, [c], x)
+        b = orc.evaluate_given(plain_fid, D, [p], x)
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+
+
+def test_block_order_with_unit_blocks(orc):
+    """At D = 3 each block is one variable and R_b = +-1, so the Ellipsoid
+    reads f = sum_i i * y_{S_i}^2 + f_opt in block order."""
+    c = orc.generate(1, 3, 8)[0]
+    assert c.blocks == [1, 1, 1]
+    assert all(abs(abs(R[0, 0]) - 1.0) < 1e-15 for R in c.R)
+    x = inputs.uniform(20, 3, 8)
+    y = x - c.o[None, :]
+    exp = sum((i + 1) * y[:, c.S[i]] ** 2 for i in range(3)) + FOPT
+    f = orc.evaluate(1, 3, 8, x)
+    assert np.abs(f - exp).max() <= 1e-12 * exp.max()
+
+
+def test_separable_permutation_invariance(orc):
+    """IDs 10 and 15 are separable: permuting x and x^opt jointly keeps f."""
+    D = 17
+    rng = np.random.default_rng(0)
+    x = inputs.uniform(30, D, 5)
+    for fid in (10, 15):
+        c = orc.generate(fid, D, 6)[0]
+        p = rng.permutation(D)
+        cp = orc.generate(fid, D, 6)[0]
+        cp.o = c.o[p].copy()
+        a = orc.evaluate_given(fid, D, [c], x)
+        b = orc.evaluate_given(fid, D, [cp], x[:, p])
+        assert np.abs(a - b).max() <= 1e-11 * np.abs(a).max()
+
+
+def test_hybrid_blocks_use_local_dimension(orc):
+    """Hybrid Function 2 (Bent Cigar | HGBat | Rastrigin, n = 3,3,4 at D = 10)
+    with R_i = I, S = identity, o = 0: the HGBat block divides by n_2 = 3."""
+    D = 10
+    c = orc.generate(24, D, 0)[0]
+    c.o = np.zeros(D)
+    c.S = np.arange(D, dtype=np.int32)
+    c.R = [np.eye(n) for n in c.blocks]
+    x = np.zeros((1, D))
+    x[0, 0:3] = [1.0, 2.0, 0.0]           # cigar z = (1,2,0): 1 + 1e6*4
+    x[0, 3:6] = [40.0, 20.0, 20.0]        # hgbat z = 0.05x - 1 = (1,0,0): 1.0
+    x[0, 6:10] = 0.0                       # rastrigin z = 0: 0
+    f = orc.evaluate_given(24, D, [c], x)[0]
+    assert abs(f - (4000001.0 + 1.0 + FOPT)) < 1e-6
+
+
+def test_composition_equal_distance_weights(orc):
+    """Composition Function 2 with o_1 = -a e_1, o_2 = +a e_1 and o_3 far
+    away: at x = 0 the first two weights are equal (same sigma, same
+    distance), the third is negligible, so F = (G_1 + b_1 + G_2 + b_2)/2."""
+    D = 4
+    comps = orc.generate(30, D, 0)
+    a = 3.0
+    comps[0].o = np.array([-a, 0, 0, 0.0])
+    comps[1].o = np.array([a, 0, 0, 0.0])
+    comps[2].o = np.array([60.0, 60, 60, 60])
+    for c in comps:
+        if c.rotated:
+            c.S = np.arange(D, dtype=np.int32)
+            c.R = [np.eye(n) for n in c.blocks]
+    x = np.zeros((1, D))
+    F = orc.evaluate_given(30, D, comps, x)[0]
+    g1 = orc.G("schwefel", 10.0 * (x[0] - comps[0].o))
+    g2 = orc.G("rastrigin", 0.0512 * (x[0] - comps[1].o))
+    # w_3 / w_1 = (3 / sqrt(4 * 3600)) * exp(-(4 * 3600 - 9) / (2 * 4 * 225))
+    r3 = (a / math.sqrt(4 * 3600.0)) * math.exp(-(4 * 3600.0 - a * a) / (2 * 4 * 225.0))
+    assert r3 < 1e-3
+    exp = 0.5 * (g1 + 0.0) + 0.5 * (g2 + 100.0) + FOPT
+    assert abs(F - exp) <= 300 * r3 + 1e-9
+
+
+def test_composition_continuous_at_member_optimum(orc):
+    """omega is one-hot at x = o_i (Eq. weight); F is continuous there.  The
+    step is tiny because the other members' G reach ~1e10 (Elliptic blocks),
+    so a weight of 1e-10 already moves F visibly."""
+    D = 10
+    for fid in (29, 31, 33, 36):
+        comps = orc.generate(fid, D, 1)
+        for k, c in enumerate(comps):
+            f0 = orc.evaluate(fid, D, 1, c.o[None, :])[0]
+            f1 = orc.evaluate(fid, D, 1, (c.o + 1e-12)[None, :])[0]
+            assert abs(f1 - f0) < 1e-3 * max(1.0, abs(f0)), (fid, k, f0, f1)
+
+
+@pytest.mark.parametrize("D", [10, 30])
+def test_lower_bound_on_random_samples(orc, D):
+    """Every function has minimum f_opt (General Setup)."""
+    for fid in range(37):
+        c0 = orc.generate(fid, D, 2)[0]
+        x = inputs.mixed(400, D, 3, center=c0.o, frac_near=0.25, sigma=1e-2)
+        f = orc.evaluate(fid, D, 2, x)
+        assert f.min() >= FOPT - 1e-9, (fid, f.min())
+
+
+@pytest.mark.parametrize("fid", list(range(23)) + list(range(29, 35)))
+def test_grid_minimum_two_dimensional(orc, fid):
+    """Brute force over a 0.5-spaced grid on [-100,100]^2 plus a fine grid
+    around x^opt: the minimum is f_opt (up to the Schwefel residual), and for
+    the well-conditioned unimodal ones (Sphere, Ellipsoid) the coarse-grid
+    argmin lies next to x^opt (ill-conditioned ones slide along a valley)."""
+    D = 2
+    g = np.arange(-100.0, 100.0 + 1e-9, 0.5)
+    X = np.stack(np.meshgrid(g, g, indexing="ij"), -1).reshape(-1, 2)
+    f = orc.evaluate(fid, D, 0, X, nthreads=4)
+    o = orc.generate(fid, D, 0)[0].o
+    h = np.linspace(-0.05, 0.05, 41)
+    Xf = o[None, :] + np.stack(np.meshgrid(h, h, indexing="ij"), -1).reshape(-1, 2)
+    ff = orc.evaluate(fid, D, 0, Xf)
+    floor = expected_at_optimum(orc, fid, D, 0) if fid in (15, 16) else FOPT
+    assert min(f.min(), ff.min()) >= min(floor, FOPT) - 1e-9
+    if fid in (15, 16):
+        return
+    assert ff.min() <= FOPT + 1e-6 or fid >= 29 or fid == 7 or fid == 17
+    if fid <= 1:
+        best = X[np.argmin(f)]
+        assert np.abs(best - o).max() <= 0.5 + 1e-9
