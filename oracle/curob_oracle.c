@@ -9,7 +9,9 @@
  * formula below is evaluated exactly as written, one rounding per operation.
  *
  * Every function is written straight from the paper's formula, in index
- * order, in FP64, with libm.  Readings of silent or garbled points:
+ * order, in FP64, with libm.  The rotation's dot products take one fused
+ * multiply-add per term (C99 fma, exactly rounded on every platform), in
+ * index order.  Readings of silent or garbled points:
  *   - functions are numbered by their Table 1 ID (the equation labels in the
  *     paper are left over from other suites);
  *   - f_opt = 100 for every function (Table 1 footer);
@@ -686,7 +688,7 @@ static double eval_component(const layout_t* L, int D, const double* o,
       const double* Rb = R + roff;
       for (int r = 0; r < n; ++r) {
         double acc = 0.0;
-        for (int c = 0; c < n; ++c) acc += Rb[(long)r * n + c] * v[c];
+        for (int c = 0; c < n; ++c) acc = fma(Rb[(long)r * n + c], v[c], acc);
         z[r] = acc + KIND_OFFSET[k];
       }
       total += oracle_G(k, z, n);
@@ -711,7 +713,7 @@ static double eval_component(const layout_t* L, int D, const double* o,
     const double* Rb = R + roff;
     for (int r = 0; r < n; ++r) {
       double acc = 0.0;
-      for (int c = 0; c < n; ++c) acc += Rb[(long)r * n + c] * v[c];
+      for (int c = 0; c < n; ++c) acc = fma(Rb[(long)r * n + c], v[c], acc);
       z[off + r] = acc + KIND_OFFSET[k];
     }
     off += n;
