@@ -1,0 +1,141 @@
+/*
+ * curob.h -- C ABI of libcurob, a GB300 (sm_103a) implementation of the cuROB
+ * real-parameter optimisation benchmark (Ding & Tan, "A CUDA-Based Real
+ * Parameter Optimization Benchmark").
+ *
+ * The library evaluates populations of N candidate vectors on the 37 test
+ * functions of the paper's Table 1 (IDs 0..36): shifted and block-rotated
+ * unimodal, multimodal, hybrid and composition functions, f_opt = 100.
+ *
+ * Conventions for every entry point:
+ *  - x is N x D, row-major (candidate n occupies x[n*D .. n*D+D-1]); out has N
+ *    entries.  Pointers passed to curob_evaluate / curob_evaluatef are DEVICE
+ *    pointers owned by the caller (Sec. 1.3 "Interface": device pointers are
+ *    passed to func_evaluate/func_evaluatef); the call is asynchronous on
+ *    `stream` (NULL = legacy default stream) and writes out[0..N-1] only.
+ *  - Argument errors are reported synchronously and launch nothing.  Errors
+ *    raised inside a kernel (a bounded wait that timed out) are latched in the
+ *    library and reported by curob_get_device_status().
+ *  - Non-finite inputs give NaN outputs, not an error.
+ *  - The library holds one instance (one D) between curob_initialize and
+ *    curob_dispose, like the paper's compile-time DIM (Sec. 1.3).  Calls are
+ *    thread-safe with respect to one another; evaluations may overlap on
+ *    different streams.
+ */
+#ifndef CUROB_H
+#define CUROB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* curob_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+  CUROB_OK = 0,
+  CUROB_ERR_NOT_INITIALIZED = 1,     /* no curob_initialize yet */
+  CUROB_ERR_ALREADY_INITIALIZED = 2, /* curob_initialize twice */
+  CUROB_ERR_INVALID_FID = 3,         /* fid outside 0..36 */
+  CUROB_ERR_INVALID_DIM = 4,         /* D < 2, or D < 10 for IDs 23..28, 35, 36 */
+  CUROB_ERR_CAPACITY = 5,            /* N > max_concurrency */
+  CUROB_ERR_NULL_POINTER = 6,        /* NULL where data is required */
+  CUROB_ERR_CUDA = 7,                /* a CUDA runtime call failed */
+  CUROB_ERR_DEVICE_TIMEOUT = 8,      /* a bounded device-side wait expired */
+  CUROB_ERR_OUT_OF_MEMORY = 9,       /* device allocation failed */
+  CUROB_ERR_INVALID_ARGUMENT = 10,   /* e.g. N < 0, host pointer where a device one is needed */
+  CUROB_ERR_UNSUPPORTED = 11         /* size outside what the chosen kernel handles */
+} curob_status;
+
+/* Rotation-contraction precision of curob_evaluatef (north of the paper: the
+ * paper evaluates FP32 plainly).  TF32X3: three TF32 tensor-core products per
+ * term (hi*hi + hi*lo + lo*hi), FP32 accumulation.  BF16X3: the same with
+ * BF16 halves.  SIMT: FP32 CUDA cores.  AUTO (default) picks per function. */
+typedef enum {
+  CUROB_PRECISION_AUTO = 0,
+  CUROB_PRECISION_TF32X3 = 1,
+  CUROB_PRECISION_BF16X3 = 2,
+  CUROB_PRECISION_SIMT = 3
+} curob_precision;
+
+/* Number of functions (Table 1). */
+#define CUROB_NUM_FUNCTIONS 37
+/* f_opt of every function (Table 1 footer). */
+#define CUROB_FOPT 100.0
+
+/* Sec. 1.3 "Interface", initialize(): builds every function's instance on the
+ * current CUDA device: shifts x^opt ~ U[-70,70]^D, a random split of the
+ * variables into blocks, one Gram-Schmidt-orthonormalised Gaussian rotation
+ * per block (General Setup), drawn from Philox4x64-10 keyed by `seed`.
+ * max_concurrency bounds N of every later evaluation (the paper's
+ * MAX_CONCURRENCY); device buffers for the host wrappers are sized by it.
+ * Errors: ALREADY_INITIALIZED, INVALID_DIM (D < 2), INVALID_ARGUMENT
+ * (max_concurrency < 1), OUT_OF_MEMORY, CUDA.  Synchronous. */
+curob_status curob_initialize(int D, int max_concurrency, uint64_t seed);
+
+/* Sec. 1.3, dispose(): releases everything curob_initialize allocated.
+ * Synchronises the device first.  Errors: NOT_INITIALIZED. */
+curob_status curob_dispose(void);
+
+/* Sec. 1.3, func_evaluate(): out[n] = f_fid(x_n) in FP64 for n < N.  x, out:
+ * device pointers (x: N*D doubles, out: N doubles).  0 <= N <= max_concurrency.
+ * Errors: NOT_INITIALIZED, INVALID_FID, INVALID_DIM, CAPACITY, NULL_POINTER,
+ * INVALID_ARGUMENT, CUDA.  Asynchronous on `stream`. */
+curob_status curob_evaluate(int fid, const double* x, int N, double* out, curob_stream_t stream);
+
+/* Sec. 1.3, func_evaluatef(): the same with FP32 x and out.  The shift x - o
+ * is taken in FP64 (o is FP64), the block rotation runs on the tensor cores
+ * in the precision set by curob_set_precision, reductions are carried in
+ * FP64 across lanes.  Same errors as curob_evaluate, plus UNSUPPORTED if a
+ * forced precision cannot handle the instance's block sizes. */
+curob_status curob_evaluatef(int fid, const float* x, int N, float* out, curob_stream_t stream);
+
+/* Sec. 1.3, h_func_evaluate / h_func_evaluatef: host-pointer wrappers.
+ * Copy x in, evaluate on the library's own stream, copy out, synchronise. */
+curob_status curob_h_evaluate(int fid, const double* x, int N, double* out);
+curob_status curob_h_evaluatef(int fid, const float* x, int N, float* out);
+
+/* Select the precision of curob_evaluatef (see curob_precision). */
+curob_status curob_set_precision(int mode);
+
+/* Synchronise `stream` and report (then clear) a latched device-side error. */
+curob_status curob_get_device_status(curob_stream_t stream);
+
+/* Human-readable name of a status code (static string). */
+const char* curob_status_string(curob_status s);
+
+/* D and max_concurrency of the current instance (host pointers). */
+curob_status curob_get_config(int* D, int* max_concurrency);
+
+/* Number of components of fid: N for a composition (Sec. 6), else 1. */
+curob_status curob_num_components(int fid, int* ncomp);
+
+/* Block layout of component comp of fid: n_blocks (<= 5) block sizes in
+ * z order, and whether the component is rotated.  Unrotated components
+ * report one block of size D.  Block sizes: (D/3, D/3, D - 2(D/3)) (General
+ * Setup), or ceil(p_i D) with the last taking the rest (Sec. 5, Eq. numbers).
+ * Host pointers. */
+curob_status curob_component_layout(int fid, int comp, int* n_blocks, int sizes[5], int* rotated);
+
+/* Copy component comp's instance data to host memory: o[D] (x^{opt,comp}),
+ * S[D] (variable indices in block order; block b takes S[off_b..off_b+n_b)),
+ * R (each rotation block n_b x n_b row-major, blocks back to back; nothing for
+ * unrotated components).  Any pointer may be NULL to skip it. */
+curob_status curob_get_component(int fid, int comp, double* o, int* S, double* R);
+
+/* Replace component comp's instance data with caller data (host pointers,
+ * layout as in curob_get_component), e.g. to evaluate published shift and
+ * rotation data.  S must be a permutation of 0..D-1; R's blocks should be
+ * orthogonal (not checked).  Synchronous.  Errors: INVALID_ARGUMENT for a
+ * bad permutation, NULL_POINTER. */
+curob_status curob_set_component(int fid, int comp, const double* o, const int* S, const double* R);
+
+/* x^opt of fid (component 0's shift; for a composition the global optimum,
+ * Sec. 6: the member with the smallest bias).  Host pointer, D doubles. */
+curob_status curob_get_optimum(int fid, double* xopt);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CUROB_H */

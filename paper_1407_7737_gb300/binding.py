@@ -1,0 +1,221 @@
+"""ctypes binding of libcurob (include/curob.h).
+
+Argument marshalling only: every function forwards to the C entry point of the
+same name, and every step of the evaluation runs in the library's CUDA
+kernels.  There is no fallback: if ``libcurob.so`` is missing or cannot be
+loaded, the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+STATUS = {
+    0: "CUROB_OK", 1: "CUROB_ERR_NOT_INITIALIZED", 2: "CUROB_ERR_ALREADY_INITIALIZED",
+    3: "CUROB_ERR_INVALID_FID", 4: "CUROB_ERR_INVALID_DIM", 5: "CUROB_ERR_CAPACITY",
+    6: "CUROB_ERR_NULL_POINTER", 7: "CUROB_ERR_CUDA", 8: "CUROB_ERR_DEVICE_TIMEOUT",
+    9: "CUROB_ERR_OUT_OF_MEMORY", 10: "CUROB_ERR_INVALID_ARGUMENT", 11: "CUROB_ERR_UNSUPPORTED",
+}
+CODES = {v: k for k, v in STATUS.items()}
+
+PRECISION_AUTO, PRECISION_TF32X3, PRECISION_BF16X3, PRECISION_SIMT = 0, 1, 2, 3
+NUM_FUNCTIONS = 37
+FOPT = 100.0
+
+# (name, restype, argtypes) of every exported entry point
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SIGS = [
+    ("curob_initialize", _I, [_I, _I, ctypes.c_uint64]),
+    ("curob_dispose", _I, []),
+    ("curob_evaluate", _I, [_I, _P, _I, _P, _P]),
+    ("curob_evaluatef", _I, [_I, _P, _I, _P, _P]),
+    ("curob_h_evaluate", _I, [_I, _P, _I, _P]),
+    ("curob_h_evaluatef", _I, [_I, _P, _I, _P]),
+    ("curob_set_precision", _I, [_I]),
+    ("curob_get_device_status", _I, [_P]),
+    ("curob_status_string", ctypes.c_char_p, [_I]),
+    ("curob_get_config", _I, [_P, _P]),
+    ("curob_num_components", _I, [_I, _P]),
+    ("curob_component_layout", _I, [_I, _I, _P, _P, _P]),
+    ("curob_get_component", _I, [_I, _I, _P, _P, _P]),
+    ("curob_set_component", _I, [_I, _I, _P, _P, _P]),
+    ("curob_get_optimum", _I, [_I, _P]),
+]
+EXPORTS = [s[0] for s in _SIGS]
+
+
+class CurobError(RuntimeError):
+    def __init__(self, fn, code):
+        self.code = code
+        super().__init__(f"{fn}: {STATUS.get(code, code)}")
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.SO
+
+
+def load(build_if_missing: bool = True):
+    """Load libcurob.so (building it if absent).  Raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.SO):
+        if not build_if_missing:
+            raise OSError(f"libcurob.so not built: {_build.SO}")
+        _build.build()
+    L = ctypes.CDLL(_build.SO)
+    for name, res, args in _SIGS:
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _call(name, *args, check=True):
+    rc = getattr(load(), name)(*args)
+    if check and rc != 0:
+        raise CurobError(name, rc)
+    return rc
+
+
+def _ptr(t):
+    """Address of a tensor / numpy array / raw integer pointer (or None)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if hasattr(t, "ctypes"):
+        return t.ctypes.data
+    raise TypeError(f"cannot take the address of {type(t)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream  # torch.cuda.Stream
+
+
+# ----- thin wrappers, same names as the C ABI -------------------------------
+def curob_initialize(D: int, max_concurrency: int, seed: int, check=True):
+    return _call("curob_initialize", D, max_concurrency, seed, check=check)
+
+
+def curob_dispose(check=True):
+    return _call("curob_dispose", check=check)
+
+
+def curob_evaluate(fid, x, N, out, stream=None, check=True):
+    return _call("curob_evaluate", fid, _ptr(x), N, _ptr(out), _stream(stream), check=check)
+
+
+def curob_evaluatef(fid, x, N, out, stream=None, check=True):
+    return _call("curob_evaluatef", fid, _ptr(x), N, _ptr(out), _stream(stream), check=check)
+
+
+def curob_h_evaluate(fid, x, N, out, check=True):
+    return _call("curob_h_evaluate", fid, _ptr(x), N, _ptr(out), check=check)
+
+
+def curob_h_evaluatef(fid, x, N, out, check=True):
+    return _call("curob_h_evaluatef", fid, _ptr(x), N, _ptr(out), check=check)
+
+
+def curob_set_precision(mode, check=True):
+    return _call("curob_set_precision", mode, check=check)
+
+
+def curob_get_device_status(stream=None, check=True):
+    return _call("curob_get_device_status", _stream(stream), check=check)
+
+
+def curob_status_string(code) -> str:
+    return load().curob_status_string(code).decode()
+
+
+def curob_get_config():
+    D, M = ctypes.c_int(), ctypes.c_int()
+    _call("curob_get_config", ctypes.addressof(D), ctypes.addressof(M))
+    return D.value, M.value
+
+
+def curob_num_components(fid):
+    n = ctypes.c_int()
+    _call("curob_num_components", fid, ctypes.addressof(n))
+    return n.value
+
+
+def curob_component_layout(fid, comp):
+    nb, rot = ctypes.c_int(), ctypes.c_int()
+    sizes = (ctypes.c_int * 5)()
+    _call("curob_component_layout", fid, comp, ctypes.addressof(nb), ctypes.addressof(sizes),
+          ctypes.addressof(rot))
+    return [sizes[i] for i in range(nb.value)], bool(rot.value)
+
+
+def curob_get_component(fid, comp):
+    """(o, S, [R_b ...]) of one component, as numpy arrays."""
+    import numpy as np
+    D, _ = curob_get_config()
+    sizes, rot = curob_component_layout(fid, comp)
+    o = np.zeros(D)
+    S = np.zeros(D, dtype=np.int32)
+    rs = sum(n * n for n in sizes) if rot else 0
+    R = np.zeros(max(rs, 1))
+    _call("curob_get_component", fid, comp, o.ctypes.data, S.ctypes.data,
+          R.ctypes.data if rot else None)
+    blocks, off = [], 0
+    if rot:
+        for n in sizes:
+            blocks.append(R[off: off + n * n].reshape(n, n).copy())
+            off += n * n
+    return o, S, blocks
+
+
+def curob_set_component(fid, comp, o, S, R_blocks, check=True):
+    import numpy as np
+    o = np.ascontiguousarray(o, dtype=np.float64)
+    S = np.ascontiguousarray(S, dtype=np.int32)
+    parts = [np.asarray(r, dtype=np.float64).reshape(-1) for r in R_blocks]
+    R = np.ascontiguousarray(np.concatenate(parts)) if parts else None
+    return _call("curob_set_component", fid, comp, o.ctypes.data, S.ctypes.data,
+                 R.ctypes.data if R is not None else None, check=check)
+
+
+def curob_get_optimum(fid):
+    import numpy as np
+    D, _ = curob_get_config()
+    o = np.zeros(D)
+    _call("curob_get_optimum", fid, o.ctypes.data)
+    return o
+
+
+# ----- tensor conveniences ---------------------------------------------------
+def evaluate(fid, x, out=None, stream=None):
+    """f(x) for a CUDA tensor x (N x D): FP64 -> curob_evaluate, FP32 ->
+    curob_evaluatef.  Returns out (allocated if None)."""
+    import torch
+    if not (x.is_cuda and x.is_contiguous() and x.dim() == 2):
+        raise ValueError("x must be a contiguous 2-D CUDA tensor")
+    N = x.shape[0]
+    if out is None:
+        out = torch.empty(N, dtype=x.dtype, device=x.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(x.device)
+    if x.dtype == torch.float64:
+        curob_evaluate(fid, x, N, out, stream)
+    elif x.dtype == torch.float32:
+        curob_evaluatef(fid, x, N, out, stream)
+    else:
+        raise TypeError("x must be float64 or float32")
+    return out

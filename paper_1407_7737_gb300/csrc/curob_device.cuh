@@ -1,0 +1,367 @@
+// curob_device.cuh -- device-side descriptors and per-function arithmetic of
+// the cuROB benchmark (Ding & Tan, "A CUDA-Based Real Parameter Optimization
+// Benchmark").  Shared by every kernel of libcurob.
+//
+// An instance of function `fid` is a list of components (one, or N for a
+// composition, Sec. 6 Eq. composition).  A component is a list of segments:
+// a segment is one rotation block b of the General Setup (or one block i of a
+// hybrid, Sec. 5 Eq. hybrid): z_b = s * R_b * (x - o)[S_b] + c.  Segments are
+// grouped into basic functions G: a plain function's G spans all three blocks
+// of its component; each hybrid block is a G of its own, of dimension n_i.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace curob {
+
+constexpr int kNumFunctions = 37;
+constexpr int kMaxComponents = 5;
+constexpr double kFopt = 100.0;  // Table 1: f_opt = 100 for every function
+constexpr double kPi = 3.14159265358979323846;
+
+// Basic functions, numbered as the Table 1 rows 0..22 they come from.
+enum Kind : int {
+  K_SPHERE = 0, K_ELLIPSOID, K_ELLIPTIC, K_DISCUS, K_CIGAR, K_POWERS,
+  K_SHARPV, K_STEP, K_WEIERSTRASS, K_GRIEWANK, K_RASTRIGIN, K_SCHAFFER7,
+  K_EGR, K_ROSENBROCK, K_SCHWEFEL, K_KATSUURA, K_LUNACEK, K_ACKLEY,
+  K_HAPPYCAT, K_HGBAT, K_SCHAFFER6, K_COUNT
+};
+
+struct Segment {
+  int n;          // variables in the block
+  int zoff;       // first position of the block in the component's z and S
+  int kind;       // basic function of the block
+  int gn;         // dimension of that function (D, or n_i in a hybrid)
+  int gpos;       // index of the block's first variable inside the function
+  int gfirst;     // the block opens a function
+  int glast;      // the block closes a function
+  int identity;   // R_b = I (unrotated component)
+  double scale;   // s of "z = R(s (x - o)) + c"
+  double offset;  // c
+  long long r_off;    // rotation block (n x n, row-major) in the rotation pools
+  long long aux_off;  // per-variable table of the block (n entries)
+  long long img_off;  // tensor-core operand image of R_b (floats)
+  int npad;           // n rounded up to the tensor-core tile
+  int comp;           // owning component (index into the component table)
+};
+
+struct Component {
+  int seg0, nseg;     // its segments in the segment table
+  long long base;     // offset of its o, S, o[S] vectors (D entries each)
+  double sigma, lambda, bias;  // composition parameters (Sec. 6)
+};
+
+struct Function {
+  int comp0, ncomp;
+  int composition;
+  int max_n;          // largest block of any component (sizes shared memory)
+};
+
+// Device view of an initialised instance.
+struct Tables {
+  const Segment* seg;
+  const Component* comp;
+  const double* o;      // shift x^opt per component
+  const int* S;         // variable indices in block order per component
+  const double* operm;  // o[S[k]] per component
+  const double* R;      // FP64 rotation blocks
+  const float* R32;     // FP32 copy of the rotation blocks
+  const double* aux;    // per-variable tables (FP64)
+  const float* aux32;   // per-variable tables (FP32)
+  const float* img;     // tensor-core operand images
+  int D;
+  int* status;          // device-side error word (0 = ok)
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) -- counter-based RNG that
+// the instance generator draws o, the permutation and the Gaussian entries
+// from.  Counter = (word/4, purpose | block << 8, fid, component), key =
+// (seed, 0), word `index % 4` of the block.
+// ---------------------------------------------------------------------------
+enum Purpose : int { P_SHIFT = 0, P_PERM = 1, P_GAUSS = 2 };
+
+__host__ __device__ inline void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+#ifdef __CUDA_ARCH__
+    uint64_t lo0 = M0 * c[0], hi0 = __umul64hi(M0, c[0]);
+    uint64_t lo1 = M1 * c[2], hi1 = __umul64hi(M1, c[2]);
+#else
+    unsigned __int128 p0 = (unsigned __int128)M0 * c[0];
+    unsigned __int128 p1 = (unsigned __int128)M1 * c[2];
+    uint64_t lo0 = (uint64_t)p0, hi0 = (uint64_t)(p0 >> 64);
+    uint64_t lo1 = (uint64_t)p1, hi1 = (uint64_t)(p1 >> 64);
+#endif
+    uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += W0; k1 += W1;
+  }
+}
+
+__host__ __device__ inline uint64_t rng_word(uint64_t seed, int purpose, int block, int fid,
+                                             int comp, uint64_t index) {
+  uint64_t c[4] = {index >> 2, (uint64_t)purpose | ((uint64_t)block << 8), (uint64_t)fid,
+                   (uint64_t)comp};
+  philox4x64_10(c, seed, 0);
+  return c[index & 3];
+}
+
+// ---------------------------------------------------------------------------
+// Per-function arithmetic.  Every basic function is "sum/product of per-
+// variable terms, then a closing map", so a kernel walks z once and keeps four
+// running values (a0, a1, a2: sums; p: product).  The neighbour-coupled
+// functions (Schaffer F7, expanded Griewank-Rosenbrock, Rosenbrock, expanded
+// Schaffer F6) add one term per consecutive pair (z_i, z_{i+1}); the two
+// "expanded" ones close the cycle with (z_D, z_1).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Acc {
+  T a0, a1, a2, p;
+};
+
+template <typename T>
+__host__ __device__ inline Acc<T> acc_zero() {
+  return Acc<T>{T(0), T(0), T(0), T(1)};
+}
+
+__host__ __device__ inline bool kind_has_pairs(int k) {
+  return k == K_SCHAFFER7 || k == K_EGR || k == K_ROSENBROCK || k == K_SCHAFFER6;
+}
+__host__ __device__ inline bool kind_is_cyclic(int k) { return k == K_EGR || k == K_SCHAFFER6; }
+
+// Math wrappers so one statement of each formula serves FP64 and FP32.
+__device__ inline double m_cos(double v) { return cos(v); }
+__device__ inline float m_cos(float v) { return cosf(v); }
+__device__ inline double m_sin(double v) { return sin(v); }
+__device__ inline float m_sin(float v) { return sinf(v); }
+__device__ inline double m_exp(double v) { return exp(v); }
+__device__ inline float m_exp(float v) { return expf(v); }
+__device__ inline double m_pow(double a, double b) { return pow(a, b); }
+__device__ inline float m_pow(float a, float b) { return powf(a, b); }
+__device__ inline double m_sqrt(double v) { return sqrt(v); }
+__device__ inline float m_sqrt(float v) { return sqrtf(v); }
+__device__ inline double m_floor(double v) { return floor(v); }
+__device__ inline float m_floor(float v) { return floorf(v); }
+__device__ inline double m_rint(double v) { return rint(v); }
+__device__ inline float m_rint(float v) { return rintf(v); }
+__device__ inline double m_fmod(double a, double b) { return fmod(a, b); }
+__device__ inline float m_fmod(float a, float b) { return fmodf(a, b); }
+__device__ inline double m_fabs(double v) { return fabs(v); }
+__device__ inline float m_fabs(float v) { return fabsf(v); }
+__device__ inline double m_cospi(double v) { return cospi(v); }
+__device__ inline float m_cospi(float v) { return cospif(v); }
+
+// Sec. 4.9, Eq. basic_schwefel: g1(w) with the two out-of-range branches.
+template <typename T>
+__device__ inline T schwefel_g1(T w, T gn) {
+  if (m_fabs(w) <= T(500)) return w * m_sin(m_sqrt(m_fabs(w)));
+  if (w > T(500)) {
+    T m = m_fmod(w, T(500));
+    T t = w - T(500);
+    return (T(500) - m) * m_sin(m_sqrt(T(500) - m)) - t * t / (T(10000) * gn);
+  }
+  T m = m_fmod(-w, T(500));
+  T t = w + T(500);
+  return (m - T(500)) * m_sin(m_sqrt(T(500) - m)) - t * t / (T(10000) * gn);
+}
+
+// Term of the pair (u, v) = (z_i, z_{i+1}) for the neighbour-coupled kinds.
+template <typename T>
+__device__ inline T pair_term(int kind, T u, T v) {
+  switch (kind) {
+    case K_SCHAFFER7: {  // Sec. 4.6: (1 + sin^2(50 w^0.2)) sqrt(w), w = |(u,v)|
+      T w = m_sqrt(u * u + v * v);
+      T t = m_sin(T(50) * m_pow(w, T(0.2)));
+      return (T(1) + t * t) * m_sqrt(w);
+    }
+    case K_EGR: {  // Sec. 4.7: g3(g2(u, v))
+      T a = u * u - v, b = u - T(1);
+      T g2 = T(100) * (a * a) + b * b;
+      return g2 * g2 / T(4000) - m_cos(g2) + T(1);
+    }
+    case K_ROSENBROCK: {  // Sec. 4.8: 100 (u^2 - v)^2 + (u - 1)^2
+      T a = u * u - v, b = u - T(1);
+      return T(100) * (a * a) + b * b;
+    }
+    case K_SCHAFFER6: {  // Sec. 4.16: g4(u, v)
+      T r2 = u * u + v * v;
+      T t = m_sin(m_sqrt(r2));
+      T d = T(1) + T(0.001) * r2;
+      return (t * t - T(0.5)) / (d * d) + T(0.5);
+    }
+    default:
+      return T(0);
+  }
+}
+
+// Weierstrass inner sum for one variable (Sec. 4.2): sum_{k=0}^{20}
+// a^k cos(2 pi b^k (z + 1/2)), a = 1/2, b = 3.  FP64 evaluates the printed
+// expression; FP32 carries the phase as frac(3^k (z + 1/2)) so that the
+// argument of the cosine stays in [0, 1).
+__device__ inline double weierstrass_inner(double z) {
+  double s = 0.0, ak = 1.0, bk = 1.0;
+  for (int k = 0; k <= 20; ++k) {
+    s += ak * cos(2.0 * kPi * bk * (z + 0.5));
+    ak *= 0.5;
+    bk *= 3.0;
+  }
+  return s;
+}
+__device__ inline float weierstrass_inner(float z) {
+  float u = z + 0.5f;
+  float t = u - floorf(u);
+  float s = 0.f, ak = 1.f;
+  for (int k = 0; k <= 20; ++k) {
+    s += ak * cospif(2.f * t);
+    ak *= 0.5f;
+    float t3 = 3.f * t;
+    t = t3 - floorf(t3);
+  }
+  return s;
+}
+
+// Weierstrass constant sum_k a^k cos(2 pi b^k / 2), in the working precision.
+template <typename T>
+__device__ inline T weierstrass_const() {
+  double c = 0.0, ak = 1.0, bk = 1.0;
+  for (int k = 0; k <= 20; ++k) {
+    c += ak * cos(2.0 * kPi * bk * 0.5);
+    ak *= 0.5;
+    bk *= 3.0;
+  }
+  return T(c);
+}
+
+// Katsuura inner sum (Sec. 4.11): sum_{j=1}^{32} |2^j z - [2^j z]| / 2^j.
+template <typename T>
+__device__ inline T katsuura_inner(T z) {
+  T s = T(0), tj = T(1);
+  for (int j = 1; j <= 32; ++j) {
+    tj = tj * T(2);
+    T v = tj * z;
+    s += m_fabs(v - m_rint(v)) / tj;
+  }
+  return s;
+}
+
+// Adds variable z (index gi inside its function of dimension gn, per-variable
+// table value `aux`, Katsuura exponent kat_e = 10/gn^1.2) to the running
+// values.  Pair terms are added by the caller.
+template <typename T>
+__device__ inline void elem_term(int kind, T z, int gi, T gn, T aux, T kat_e, Acc<T>& a) {
+  switch (kind) {
+    case K_SPHERE: a.a0 += z * z; break;
+    case K_ELLIPSOID: a.a0 += T(gi + 1) * (z * z); break;
+    case K_ELLIPTIC: a.a0 += aux * (z * z); break;  // aux = (1e6)^(i/(n-1))
+    case K_DISCUS:
+    case K_CIGAR:
+    case K_SHARPV:
+      if (gi == 0) a.a1 += z * z; else a.a0 += z * z;
+      break;
+    case K_POWERS: a.a0 += m_pow(m_fabs(z), aux); break;  // aux = 2 + 4 i/(n-1)
+    case K_STEP: { T t = m_floor(z + T(0.5)); a.a0 += t * t; } break;
+    case K_WEIERSTRASS: a.a0 += weierstrass_inner(z); break;
+    case K_GRIEWANK:
+      a.a0 += z * z / T(4000);
+      a.p *= m_cos(z / aux);  // aux = sqrt(i)
+      break;
+    case K_RASTRIGIN: a.a0 += z * z - T(10) * m_cos(T(2) * T(kPi) * z) + T(10); break;
+    case K_SCHWEFEL: a.a0 += schwefel_g1(z + T(420.9687462275036), gn); break;
+    case K_KATSUURA: a.p *= m_pow(T(1) + T(gi + 1) * katsuura_inner(z), kat_e); break;
+    case K_LUNACEK: {
+      T u = z - T(2.5), v = z + T(2.5);
+      a.a0 += u * u;
+      a.a1 += v * v;
+      a.a2 += m_cos(T(2) * T(kPi) * u);
+    } break;
+    case K_ACKLEY:
+      a.a0 += z * z;
+      a.a1 += m_cos(T(2) * T(kPi) * z);
+      break;
+    case K_HAPPYCAT:
+    case K_HGBAT:
+      a.a0 += z * z;
+      a.a1 += z;
+      break;
+    default: break;  // pair kinds: only pair terms
+  }
+}
+
+// Closing map of each basic function; gn = its dimension.  Returns the value
+// without f_opt.  Works in FP64 whatever the working precision.
+__device__ inline double finalize(int kind, double a0, double a1, double a2, double p, int gn_i) {
+  if (gn_i == 0) return 0.0;
+  const double gn = (double)gn_i;
+  switch (kind) {
+    case K_DISCUS: return 1.0e6 * a1 + a0;                 // Sec. 3.4
+    case K_CIGAR: return a1 + 1.0e6 * a0;                  // Sec. 3.5
+    case K_SHARPV: return a1 + 100.0 * sqrt(a0);           // Sec. 3.7
+    case K_POWERS: return sqrt(a0);                        // Sec. 3.6
+    case K_WEIERSTRASS: return a0 - gn * weierstrass_const<double>();  // Sec. 4.2
+    case K_GRIEWANK: return a0 - p + 1.0;                  // Sec. 4.3
+    case K_SCHAFFER7: {                                    // Sec. 4.6
+      if (gn_i < 2) return 0.0;
+      double m = a0 / (gn - 1.0);
+      return m * m;
+    }
+    case K_SCHWEFEL: return 418.9829 * gn - a0;            // Sec. 4.9
+    case K_KATSUURA: {                                     // Sec. 4.11
+      double c = 10.0 / (gn * gn);
+      return c * p - c;
+    }
+    case K_LUNACEK: {                                      // Sec. 4.12
+      double t2 = 1.0 * gn + 0.9 * a1;
+      return (a0 < t2 ? a0 : t2) + 10.0 * (gn - a2);
+    }
+    case K_ACKLEY:                                         // Sec. 4.13
+      return -20.0 * exp(-0.2 * sqrt(a0 / gn)) - exp(a1 / gn) + 20.0 + exp(1.0);
+    case K_HAPPYCAT:                                       // Sec. 4.14
+      return pow(fabs(a0 - gn), 0.25) + (0.5 * a0 + a1) / gn + 0.5;
+    case K_HGBAT:                                          // Sec. 4.15
+      return pow(fabs(a0 * a0 - a1 * a1), 0.5) + (0.5 * a0 + a1) / gn + 0.5;
+    default:  // sphere, ellipsoid, elliptic, step, rastrigin, EGR, rosenbrock, F6
+      return a0;
+  }
+}
+
+// Composition (Sec. 6, Eq. composition and Eq. weight): sum_i omega_i
+// (lambda_i G_i + bias_i), omega = w / sum w, w_i = exp(-d_i^2/(2 D sigma_i^2))
+// / d_i; one-hot at the first i with d_i = 0.  FP64.
+__device__ inline double compose(const Component* comps, int nc, const double* G, const double* d2,
+                                 int D) {
+  int hit = -1;
+  for (int c = 0; c < nc; ++c)
+    if (d2[c] == 0.0 && hit < 0) hit = c;
+  if (hit >= 0) return comps[hit].lambda * G[hit] + comps[hit].bias;
+  double w[kMaxComponents], W = 0.0;
+  for (int c = 0; c < nc; ++c) {
+    double s = comps[c].sigma;
+    w[c] = (1.0 / sqrt(d2[c])) * exp(-d2[c] / (2.0 * (double)D * s * s));
+    W += w[c];
+  }
+  double F = 0.0;
+  if (W > 0.0) {
+    for (int c = 0; c < nc; ++c) F += (w[c] / W) * (comps[c].lambda * G[c] + comps[c].bias);
+    return F;
+  }
+  // all weights underflowed (far outside the box): the same ratio in logs
+  double lw[kMaxComponents], mx = -1e300;
+  for (int c = 0; c < nc; ++c) {
+    double s = comps[c].sigma;
+    lw[c] = -0.5 * log(d2[c]) - d2[c] / (2.0 * (double)D * s * s);
+    mx = lw[c] > mx ? lw[c] : mx;
+  }
+  double Z = 0.0;
+  for (int c = 0; c < nc; ++c) Z += exp(lw[c] - mx);
+  for (int c = 0; c < nc; ++c) F += (exp(lw[c] - mx) / Z) * (comps[c].lambda * G[c] + comps[c].bias);
+  return F;
+}
+
+// Device error codes written to Tables::status.
+enum DeviceError : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BAD_ARG = 2 };
+
+}  // namespace curob

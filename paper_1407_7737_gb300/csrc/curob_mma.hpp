@@ -1,0 +1,30 @@
+// curob_mma.hpp -- the tensor-core (tcgen05) evaluator of curob_evaluatef.
+#pragma once
+
+#include <vector>
+
+#include "../../include/curob.h"
+#include "curob_internal.hpp"
+
+namespace curob {
+
+struct MmaPlan {
+  float* img = nullptr;      // operand images of every rotation block
+  long long img_floats = 0;
+  bool ready = false;
+};
+
+// Lays out and fills the operand images (sets Segment::img_off / npad).
+curob_status mma_prepare(MmaPlan& p, std::vector<Segment>& segs, const Tables& tb, float* prev);
+// Rebuilds the images of the given segments after their R changed.
+curob_status mma_refresh(MmaPlan& p, const std::vector<Segment>& segs, const std::vector<int>& ids,
+                         const Tables& tb);
+void mma_release(MmaPlan& p);
+// True when every block of F fits the tensor-core kernel.
+bool mma_supports(const MmaPlan& p, const Function& F);
+// Precision AUTO picks for F (CUROB_PRECISION_TF32X3 or _BF16X3).
+int mma_auto_mode(const MmaPlan& p, const Function& F);
+cudaError_t launch_mma(const MmaPlan& p, const Tables& tb, const Function& F, bool bf16,
+                       const float* x, int N, float* out, cudaStream_t st);
+
+}  // namespace curob
