@@ -271,10 +271,12 @@ static double g_weierstrass(const double* z, int n) {
   const int kmax = 20;
   double s = 0.0;
   for (int i = 0; i < n; ++i) {
+    double inner = 0.0; /* the bracketed sum over k of Eq. weierstrass */
     for (int k = 0; k <= kmax; ++k) {
       double ak = pow(a, (double)k), bk = pow(b, (double)k);
-      s += ak * cos(2.0 * PI_D * bk * (z[i] + 0.5));
+      inner += ak * cos(2.0 * PI_D * bk * (z[i] + 0.5));
     }
+    s += inner;
   }
   double c = 0.0;
   for (int k = 0; k <= kmax; ++k) {
