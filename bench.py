@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--precision", default="auto", choices=["auto", "tf32x3", "bf16x3", "simt"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the FP64 and forced-precision side measurements")
+    ap.add_argument("--profile-fid", type=int, default=None,
+                    help="profiling case: two launches of one function, no JSON")
     return ap.parse_args()
 
 
@@ -175,6 +179,15 @@ def run_curob(args):
     OUT = torch.empty((NFUN, N), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    if args.profile_fid is not None:
+        for _ in range(2):
+            cu.curob_evaluatef(args.profile_fid, X[args.profile_fid], N, OUT[args.profile_fid],
+                               stream)
+        torch.cuda.synchronize()
+        cu.curob_get_device_status(stream)
+        cu.curob_dispose()
+        return
+
     def step(evs=None):
         for fid in range(NFUN):
             if evs is not None:
@@ -212,35 +225,68 @@ def run_curob(args):
     evals = NFUN * N * world
     value = evals / (ms_step / 1e3)
 
-    # FP64 path on the same workload (one pass; FP64 inputs per function)
-    fp64 = None
-    if rank == 0:
-        x64 = torch.empty((N, D), dtype=torch.float64, device=dev)
-        o64 = torch.empty(N, dtype=torch.float64, device=dev)
-        x64.copy_(X[0])
-        for fid in range(NFUN):  # warm
-            cu.curob_evaluate(fid, x64, N, o64, stream)
-        torch.cuda.synchronize()
+    modes = [cu.curob_query_precision(f) for f in range(NFUN)]
+
+    def timed_pass(mode):
+        """Step time (ms) of all 37 functions with the precision forced."""
+        cu.curob_set_precision(mode)
+        step()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
         a.record(stream)
-        for fid in range(NFUN):
-            cu.curob_evaluate(fid, x64, N, o64, stream)
+        step()
         b.record(stream)
         torch.cuda.synchronize()
-        fp64 = NFUN * N / (a.elapsed_time(b) / 1e3)
+        cu.curob_set_precision(0)
+        return a.elapsed_time(b)
 
-    # roofline of the dominant kernel: the rotation contraction
+    extra = {}
+    fp64 = None
+    if rank == 0 and not args.no_extra:
+        for name, m in (("tf32x3", 1), ("bf16x3", 2), ("simt", 3)):
+            extra[name + "_evals_s"] = round(NFUN * N / (timed_pass(m) / 1e3), 1)
+        # FP64 path on the same workload (FP64 copy of the batches)
+        x64 = torch.empty((N, D), dtype=torch.float64, device=dev)
+        o64 = torch.empty(N, dtype=torch.float64, device=dev)
+        fp64_ms = 0.0
+        for fid in range(NFUN):
+            x64.copy_(X[fid])
+            cu.curob_evaluate(fid, x64, N, o64, stream)  # warm
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            cu.curob_evaluate(fid, x64, N, o64, stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            fp64_ms += a.elapsed_time(b)
+        fp64 = NFUN * N / (fp64_ms / 1e3)
+
+    # roofline of the dominant kernel (the path holding most of the step)
     pk, src = peaks()
     flops = np.array([algorithmic_flops(cu, f) * N for f in range(NFUN)], dtype=np.float64)
-    rot = flops > 0
-    achieved = flops[rot].sum() / (launch_ms[rot].sum() / 1e3) / 1e12
-    tf32_peak = pk["bf16_tflops"] * (1.1 / 2.25)  # TF32 dense = bf16 x nominal ratio
-    roof = {"bound": "tensor", "achieved": round(achieved, 2),
-            "peak": round(tf32_peak, 1), "unit": "TFLOP/s",
-            "frac": round(achieved / tf32_peak, 4), "traffic": None,
-            "peak_source": f"{src} bf16 x 1.1/2.25 (TF32/BF16 nominal)",
-            "note": "algorithmic flops 2*sum(n_b^2) per candidate; 3 split products execute 3x"}
+    mma = np.array([m in (1, 2) for m in modes])
+    t_mma, t_simt = launch_ms[mma].sum(), launch_ms[~mma].sum()
+    if t_mma >= t_simt:
+        sel = mma & (flops > 0)
+        achieved = flops[sel].sum() / (launch_ms[sel].sum() / 1e3) / 1e12
+        peak = pk["bf16_tflops"] * (1.1 / 2.25)  # TF32 dense = bf16 x nominal ratio
+        roof = {"bound": "tensor", "kernel": "mma_eval_kernel (tcgen05 TF32x3)",
+                "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": f"{src} bf16 x 1.1/2.25 (TF32/BF16 nominal ratio)",
+                "share_of_step": round(t_mma / launch_ms.sum(), 3),
+                "note": "algorithmic flops 2*sum(n_b^2) per candidate; three split products execute 3x"}
+    else:
+        sel = (~mma) & (flops > 0)
+        achieved = flops[sel].sum() / (launch_ms[sel].sum() / 1e3) / 1e12
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 FMA lanes x 2 flop x max SM clock
+        roof = {"bound": "alu", "kernel": "eval_simt_f32_kernel (compensated FP32)",
+                "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "share_of_step": round(t_simt / launch_ms.sum(), 3),
+                "note": "algorithmic flops 2*sum(n_b^2) per candidate; the compensated dot product executes ~6x"}
 
     e2e = None
     if not args.no_e2e:
@@ -276,7 +322,10 @@ def run_curob(args):
                        "l2": "37 distinct input batches (2.4 GB) > L2 per step",
                        "parallelism": f"replicas x{world} (independent batches)"},
             "fp64_evals_s": round(fp64, 1) if fp64 else None,
+            **extra,
             "per_function_ms": [round(v, 4) for v in launch_ms.tolist()],
+            "per_function_path": ["tf32x3" if m == 1 else "bf16x3" if m == 2 else "simt"
+                                  for m in modes],
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk.summary(), "gpu_launches": gpu_launches,
         }

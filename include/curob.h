@@ -99,6 +99,12 @@ curob_status curob_h_evaluatef(int fid, const float* x, int N, float* out);
 /* Select the precision of curob_evaluatef (see curob_precision). */
 curob_status curob_set_precision(int mode);
 
+/* The precision curob_evaluatef will use for fid under the current setting
+ * (AUTO resolved): CUROB_PRECISION_TF32X3, _BF16X3 or _SIMT.  Host pointer.
+ * Errors: NOT_INITIALIZED, INVALID_FID, INVALID_DIM, NULL_POINTER,
+ * UNSUPPORTED (a forced tensor-core precision the instance cannot use). */
+curob_status curob_query_precision(int fid, int* mode);
+
 /* Synchronise `stream` and report (then clear) a latched device-side error. */
 curob_status curob_get_device_status(curob_stream_t stream);
 

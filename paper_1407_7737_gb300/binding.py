@@ -35,6 +35,7 @@ _SIGS = [
     ("curob_h_evaluate", _I, [_I, _P, _I, _P]),
     ("curob_h_evaluatef", _I, [_I, _P, _I, _P]),
     ("curob_set_precision", _I, [_I]),
+    ("curob_query_precision", _I, [_I, _P]),
     ("curob_get_device_status", _I, [_P]),
     ("curob_status_string", ctypes.c_char_p, [_I]),
     ("curob_get_config", _I, [_P, _P]),
@@ -133,6 +134,12 @@ def curob_h_evaluatef(fid, x, N, out, check=True):
 
 def curob_set_precision(mode, check=True):
     return _call("curob_set_precision", mode, check=check)
+
+
+def curob_query_precision(fid):
+    m = ctypes.c_int()
+    _call("curob_query_precision", fid, ctypes.addressof(m))
+    return m.value
 
 
 def curob_get_device_status(stream=None, check=True):

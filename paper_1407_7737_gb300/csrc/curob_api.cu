@@ -144,7 +144,7 @@ struct State {
   Component* d_comp = nullptr;
   double *d_o = nullptr, *d_operm = nullptr, *d_R = nullptr, *d_aux = nullptr;
   int* d_S = nullptr;
-  float *d_R32 = nullptr, *d_aux32 = nullptr, *d_img = nullptr;
+  float *d_R32 = nullptr, *d_R32lo = nullptr, *d_aux32 = nullptr, *d_img = nullptr;
   int* d_status = nullptr;
   long long r_total = 0, aux_total = 0, img_total = 0;
   void* d_hx = nullptr;   // host-wrapper staging (max_conc x D doubles)
@@ -164,6 +164,7 @@ Tables tables() {
   t.operm = g.d_operm;
   t.R = g.d_R;
   t.R32 = g.d_R32;
+  t.R32lo = g.d_R32lo;
   t.aux = g.d_aux;
   t.aux32 = g.d_aux32;
   t.img = g.d_img;
@@ -174,13 +175,13 @@ Tables tables() {
 
 void free_all() {
   cudaFree(g.d_seg); cudaFree(g.d_comp); cudaFree(g.d_o); cudaFree(g.d_operm);
-  cudaFree(g.d_R); cudaFree(g.d_aux); cudaFree(g.d_S); cudaFree(g.d_R32);
-  cudaFree(g.d_aux32); cudaFree(g.d_img); cudaFree(g.d_status); cudaFree(g.d_hx);
+  cudaFree(g.d_R); cudaFree(g.d_aux); cudaFree(g.d_S); cudaFree(g.d_R32); cudaFree(g.d_R32lo);
+  cudaFree(g.d_aux32); cudaFree(g.d_status); cudaFree(g.d_hx);  // d_img belongs to g.mma
   cudaFree(g.d_hout);
   if (g.hstream) cudaStreamDestroy(g.hstream);
   mma_release(g.mma);
   g.d_seg = nullptr; g.d_comp = nullptr; g.d_o = g.d_operm = g.d_R = g.d_aux = nullptr;
-  g.d_S = nullptr; g.d_R32 = g.d_aux32 = g.d_img = nullptr; g.d_status = nullptr;
+  g.d_S = nullptr; g.d_R32 = g.d_R32lo = g.d_aux32 = g.d_img = nullptr; g.d_status = nullptr;
   g.d_hx = g.d_hout = nullptr; g.hstream = nullptr;
   g.segs.clear(); g.comps.clear(); g.chost.clear();
   for (int f = 0; f < kNumFunctions; ++f) g.func_ok[f] = false;
@@ -202,6 +203,7 @@ void build_tables(int D) {
     F.ncomp = ci.n;
     F.composition = fid >= 29;
     F.max_n = 0;
+    F.sensitive = 0;
     for (int c = 0; c < ci.n; ++c) {
       const Member& m = ci.m[c];
       CompHost ch;
@@ -250,6 +252,7 @@ void build_tables(int D) {
         s.npad = 0;
         s.comp = (int)g.comps.size();
         F.max_n = std::max(F.max_n, s.n);
+        if (kind_is_sensitive(s.kind)) F.sensitive = 1;
         ch.segs.push_back((int)g.segs.size());
         g.segs.push_back(s);
       }
@@ -343,7 +346,7 @@ curob_status generate_all() {
   if (rc == CUROB_OK)
     fail(launch_gauss_gs(d_gj, (int)gj.size(), max_n, g.seed, g.d_R, g.d_status, 0));
   if (rc == CUROB_OK) fail(launch_aux(d_aj, (int)aj.size(), g.d_aux, g.d_aux32, 0));
-  if (rc == CUROB_OK) fail(launch_to_f32(g.d_R, g.d_R32, g.r_total, 0));
+  if (rc == CUROB_OK) fail(launch_split_f32(g.d_R, g.d_R32, g.d_R32lo, g.r_total, 0));
   if (rc == CUROB_OK) fail(cudaDeviceSynchronize());
   cudaFree(d_pj); cudaFree(d_gj); cudaFree(d_aj); cudaFree(d_words); cudaFree(d_mark);
   if (rc == CUROB_OK) {
@@ -374,6 +377,16 @@ bool device_accessible(const void* p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// The precision curob_evaluatef uses for F (AUTO resolved), or -1 when a
+// forced tensor-core precision cannot take F's block sizes.
+int resolve_precision(const Function& F) {
+  int mode = g.precision;
+  const bool mma_ok = mma_supports(g.mma, F);
+  if ((mode == CUROB_PRECISION_TF32X3 || mode == CUROB_PRECISION_BF16X3) && !mma_ok) return -1;
+  if (mode == CUROB_PRECISION_AUTO) mode = mma_ok ? mma_auto_mode(g.mma, F) : CUROB_PRECISION_SIMT;
+  return mode;
 }
 
 int find_comp(int fid, int comp) {
@@ -428,6 +441,7 @@ curob_status curob_initialize(int D, int max_concurrency, uint64_t seed) {
             alloc((void**)&g.d_S, sizeof(int) * (size_t)nc * D) &&
             alloc((void**)&g.d_R, sizeof(double) * (size_t)g.r_total) &&
             alloc((void**)&g.d_R32, sizeof(float) * (size_t)g.r_total) &&
+            alloc((void**)&g.d_R32lo, sizeof(float) * (size_t)g.r_total) &&
             alloc((void**)&g.d_aux, sizeof(double) * (size_t)g.aux_total) &&
             alloc((void**)&g.d_aux32, sizeof(float) * (size_t)g.aux_total) &&
             alloc((void**)&g.d_status, sizeof(int)) &&
@@ -486,11 +500,8 @@ curob_status curob_evaluatef(int fid, const float* x, int N, float* out, curob_s
   if (rc != CUROB_OK || N == 0) return rc;
   if (!device_accessible(x) || !device_accessible(out)) return CUROB_ERR_INVALID_ARGUMENT;
   const Function& F = g.func[fid];
-  int mode = g.precision;
-  const bool mma_ok = mma_supports(g.mma, F);
-  if ((mode == CUROB_PRECISION_TF32X3 || mode == CUROB_PRECISION_BF16X3) && !mma_ok)
-    return CUROB_ERR_UNSUPPORTED;
-  if (mode == CUROB_PRECISION_AUTO) mode = mma_ok ? mma_auto_mode(g.mma, F) : CUROB_PRECISION_SIMT;
+  const int mode = resolve_precision(F);
+  if (mode < 0) return CUROB_ERR_UNSUPPORTED;
   cudaError_t e;
   if (mode == CUROB_PRECISION_SIMT)
     e = launch_simt_f32(tables(), F, x, N, out, (cudaStream_t)stream);
@@ -534,6 +545,17 @@ curob_status curob_set_precision(int mode) {
   if (mode < CUROB_PRECISION_AUTO || mode > CUROB_PRECISION_SIMT)
     return CUROB_ERR_INVALID_ARGUMENT;
   g.precision = mode;
+  return CUROB_OK;
+}
+
+curob_status curob_query_precision(int fid, int* mode) {
+  if (!g.init) return CUROB_ERR_NOT_INITIALIZED;
+  if (fid < 0 || fid >= kNumFunctions) return CUROB_ERR_INVALID_FID;
+  if (!g.func_ok[fid]) return CUROB_ERR_INVALID_DIM;
+  if (!mode) return CUROB_ERR_NULL_POINTER;
+  const int m = resolve_precision(g.func[fid]);
+  if (m < 0) return CUROB_ERR_UNSUPPORTED;
+  *mode = m;
   return CUROB_OK;
 }
 
@@ -637,7 +659,7 @@ curob_status curob_set_component(int fid, int comp, const double* o, const int* 
       const Segment& s = g.segs[sid];
       const size_t nn = (size_t)s.n * s.n;
       CU(cudaMemcpy(g.d_R + s.r_off, R + off, sizeof(double) * nn, cudaMemcpyHostToDevice));
-      CU(launch_to_f32(g.d_R + s.r_off, g.d_R32 + s.r_off, (long long)nn, 0));
+      CU(launch_split_f32(g.d_R + s.r_off, g.d_R32 + s.r_off, g.d_R32lo + s.r_off, (long long)nn, 0));
       off += (long long)nn;
     }
   }

@@ -56,6 +56,10 @@ struct Function {
   int comp0, ncomp;
   int composition;
   int max_n;          // largest block of any component (sizes shared memory)
+  int sensitive;      // has a kind whose value magnifies contraction error:
+                      // Discus (10^6 z_1^2), Weierstrass (3^k phases),
+                      // expanded Griewank-Rosenbrock (cos of g2 ~ 1e4),
+                      // Katsuura (2^j phases)
 };
 
 // Device view of an initialised instance.
@@ -66,7 +70,8 @@ struct Tables {
   const int* S;         // variable indices in block order per component
   const double* operm;  // o[S[k]] per component
   const double* R;      // FP64 rotation blocks
-  const float* R32;     // FP32 copy of the rotation blocks
+  const float* R32;     // FP32 rounding of the rotation blocks (hi word)
+  const float* R32lo;   // R - R32 rounded to FP32 (lo word)
   const double* aux;    // per-variable tables (FP64)
   const float* aux32;   // per-variable tables (FP32)
   const float* img;     // tensor-core operand images
@@ -132,6 +137,9 @@ __host__ __device__ inline bool kind_has_pairs(int k) {
   return k == K_SCHAFFER7 || k == K_EGR || k == K_ROSENBROCK || k == K_SCHAFFER6;
 }
 __host__ __device__ inline bool kind_is_cyclic(int k) { return k == K_EGR || k == K_SCHAFFER6; }
+__host__ __device__ inline bool kind_is_sensitive(int k) {
+  return k == K_DISCUS || k == K_WEIERSTRASS || k == K_EGR || k == K_KATSUURA;
+}
 
 // Math wrappers so one statement of each formula serves FP64 and FP32.
 __device__ inline double m_cos(double v) { return cos(v); }
@@ -211,15 +219,20 @@ __device__ inline double weierstrass_inner(double z) {
   }
   return s;
 }
+// FP32: the phase frac(3^k (z + 1/2)) is carried exactly as a 40-bit binary
+// fraction (z is exact in it for |z| >= 2^-17), multiplied by 3 modulo 1 in
+// integer arithmetic, so rounding adds no phase error however large 3^k is;
+// cos(2 pi t) = -cos(2 pi (t - 1/2)) with the argument in [-pi, pi).
 __device__ inline float weierstrass_inner(float z) {
-  float u = z + 0.5f;
-  float t = u - floorf(u);
+  const long long Z = __float2ll_rn(z * 1099511627776.0f);          // z 2^40
+  unsigned long long P = (unsigned long long)(Z + 549755813888LL);   // (z + 1/2) 2^40
   float s = 0.f, ak = 1.f;
+#pragma unroll
   for (int k = 0; k <= 20; ++k) {
-    s += ak * cospif(2.f * t);
+    const float t = (float)((unsigned)(P >> 16) & 0xFFFFFFu) * 5.9604644775390625e-8f;
+    s = fmaf(-ak, __cosf(6.28318530717958647692f * (t - 0.5f)), s);
     ak *= 0.5f;
-    float t3 = 3.f * t;
-    t = t3 - floorf(t3);
+    P *= 3ull;  // the low 40 bits hold frac(3^{k+1} (z + 1/2))
   }
   return s;
 }
@@ -248,44 +261,117 @@ __device__ inline T katsuura_inner(T z) {
   return s;
 }
 
-// Adds variable z (index gi inside its function of dimension gn, per-variable
-// table value `aux`, Katsuura exponent kat_e = 10/gn^1.2) to the running
-// values.  Pair terms are added by the caller.
-template <typename T>
-__device__ inline void elem_term(int kind, T z, int gi, T gn, T aux, T kat_e, Acc<T>& a) {
+// ---------------------------------------------------------------------------
+// FP64 terms.  The FP64 path evaluates each variable's term(s) with exactly
+// the expression of the formula, then sums them per candidate in index
+// order, so that its sums round like a sequential evaluation of the printed
+// formula.  Array a of a kind is a sum, except Griewank's a = 1 and
+// Katsuura's a = 0, which are products.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int f64_num_terms(int kind) {
   switch (kind) {
-    case K_SPHERE: a.a0 += z * z; break;
-    case K_ELLIPSOID: a.a0 += T(gi + 1) * (z * z); break;
-    case K_ELLIPTIC: a.a0 += aux * (z * z); break;  // aux = (1e6)^(i/(n-1))
-    case K_DISCUS:
-    case K_CIGAR:
-    case K_SHARPV:
-      if (gi == 0) a.a1 += z * z; else a.a0 += z * z;
+    case K_GRIEWANK: case K_ACKLEY: case K_HAPPYCAT: case K_HGBAT: return 2;
+    case K_LUNACEK: return 3;
+    default: return 1;
+  }
+}
+__host__ __device__ inline bool f64_term_is_product(int kind, int a) {
+  return (kind == K_GRIEWANK && a == 1) || (kind == K_KATSUURA && a == 0);
+}
+
+// Term a of variable z (index gi in its function of dimension gn).  For the
+// neighbour-coupled kinds the term is the pair (z, znext).
+__device__ inline double term_f64(int kind, int a, double z, double znext, int gi, double gn,
+                                  double aux, double kat_e) {
+  switch (kind) {
+    case K_SPHERE: case K_DISCUS: case K_CIGAR: case K_SHARPV: return z * z;
+    case K_ELLIPSOID: return (double)(gi + 1) * (z * z);      // Sec. 3.2
+    case K_ELLIPTIC: return aux * (z * z);                     // Sec. 3.3
+    case K_POWERS: return pow(fabs(z), aux);                   // Sec. 3.6
+    case K_STEP: { double t = floor(z + 0.5); return t * t; }  // Sec. 4.1
+    case K_WEIERSTRASS: return weierstrass_inner(z);           // Sec. 4.2
+    case K_GRIEWANK: return a == 0 ? z * z / 4000.0 : cos(z / aux);  // Sec. 4.3
+    case K_RASTRIGIN: return z * z - 10.0 * cos(2.0 * kPi * z) + 10.0;  // Sec. 4.4
+    case K_SCHWEFEL: return schwefel_g1(z + 420.9687462275036, gn);     // Sec. 4.9
+    case K_KATSUURA: return pow(1.0 + (double)(gi + 1) * katsuura_inner(z), kat_e);  // 4.11
+    case K_LUNACEK: {                                          // Sec. 4.12
+      if (a == 0) { double u = z - 2.5; return u * u; }
+      if (a == 1) { double v = z - (-2.5); return v * v; }
+      return cos(2.0 * kPi * (z - 2.5));
+    }
+    case K_ACKLEY: return a == 0 ? z * z : cos(2.0 * kPi * z);  // Sec. 4.13
+    case K_HAPPYCAT: case K_HGBAT: return a == 0 ? z * z : z;   // Sec. 4.14, 4.15
+    default: return pair_term<double>(kind, z, znext);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 terms (tensor-core and CUDA-core FP32 paths).  z is the transformed
+// variable, u = z - c its value before the offset c (exact, no rounding of
+// c), so that forms that cancel near the optimum can be rewritten in u:
+//   HappyCat  sum z^2 - D           = sum u (u - 2)          (c = -1)
+//             (sum z^2/2 + sum z)/D + 1/2 = sum u^2 / (2 D)
+//   HGBat     (sum z^2)^2 - (sum z)^2 = sum z(z-1) * sum z(z+1)
+//                                     = sum (u-1)(u-2) * sum (u-1) u
+//   Lunacek   z - mu_1 = u,  z - mu_2 = u + 5                (c = 2.5)
+// Cosines of 2 pi v are taken as cospi(2 v) (exact argument reduction).
+// ---------------------------------------------------------------------------
+// Modified Schwefel term 418.9829 - g1(z + c), c = 420.9687462275036, in
+// FP32 without the cancellation that makes the sum over D such terms lose
+// digits near the optimum: for 0 < w = z + c <= 500,
+//   g1(w) - g1(c) = 2 w cos((sqrt w + sqrt c)/2) sin(z / (2 (sqrt w + sqrt c)))
+//                   + z sin(sqrt c),
+// and 418.9829 - g1(c) = 1.27275662959398e-5 (constants to 40 digits).  Other
+// branches use the plain expression.
+__device__ inline float schwefel_term_f32(float z, float gn) {
+  const float w = z + 420.96875f;  // sqrt and prefactor only: z enters exactly below
+  if (w > 0.f && w <= 500.f) {
+    const float sc = 20.51752290671326630f;      // sqrt(c)
+    const float ssc = 0.99528264515390726719f;   // sin(sqrt(c))
+    const float sum = sqrtf(w) + sc;
+    const float dg = 2.f * w * cosf(0.5f * sum) * sinf(z / (2.f * sum)) + z * ssc;
+    return 1.2727566295939802e-5f - dg;
+  }
+  return 418.9829f - schwefel_g1(z + 420.9687462275036f, gn);
+}
+
+__device__ inline void elem_term_f32(int kind, float z, float u, int gi, float gn, float aux,
+                                     float kat_e, Acc<float>& a) {
+  switch (kind) {
+    case K_SPHERE: a.a0 = fmaf(z, z, a.a0); break;
+    case K_ELLIPSOID: a.a0 = fmaf((float)(gi + 1), z * z, a.a0); break;
+    case K_ELLIPTIC: a.a0 = fmaf(aux, z * z, a.a0); break;
+    case K_DISCUS: case K_CIGAR: case K_SHARPV:
+      if (gi == 0) a.a1 = fmaf(z, z, a.a1); else a.a0 = fmaf(z, z, a.a0);
       break;
-    case K_POWERS: a.a0 += m_pow(m_fabs(z), aux); break;  // aux = 2 + 4 i/(n-1)
-    case K_STEP: { T t = m_floor(z + T(0.5)); a.a0 += t * t; } break;
+    case K_POWERS: a.a0 += powf(fabsf(z), aux); break;
+    case K_STEP: { float t = floorf(z + 0.5f); a.a0 = fmaf(t, t, a.a0); } break;
     case K_WEIERSTRASS: a.a0 += weierstrass_inner(z); break;
     case K_GRIEWANK:
-      a.a0 += z * z / T(4000);
-      a.p *= m_cos(z / aux);  // aux = sqrt(i)
+      a.a0 = fmaf(z, z * (1.0f / 4000.0f), a.a0);
+      a.p *= cosf(z / aux);
       break;
-    case K_RASTRIGIN: a.a0 += z * z - T(10) * m_cos(T(2) * T(kPi) * z) + T(10); break;
-    case K_SCHWEFEL: a.a0 += schwefel_g1(z + T(420.9687462275036), gn); break;
-    case K_KATSUURA: a.p *= m_pow(T(1) + T(gi + 1) * katsuura_inner(z), kat_e); break;
+    case K_RASTRIGIN: a.a0 += fmaf(z, z, 10.0f - 10.0f * cospif(2.0f * z)); break;
+    case K_SCHWEFEL: a.a0 += schwefel_term_f32(z, gn); break;
+    case K_KATSUURA: a.p *= powf(fmaf((float)(gi + 1), katsuura_inner(z), 1.0f), kat_e); break;
     case K_LUNACEK: {
-      T u = z - T(2.5), v = z + T(2.5);
-      a.a0 += u * u;
-      a.a1 += v * v;
-      a.a2 += m_cos(T(2) * T(kPi) * u);
+      float v = u + 5.0f;
+      a.a0 = fmaf(u, u, a.a0);
+      a.a1 = fmaf(v, v, a.a1);
+      a.a2 += cospif(2.0f * u);
     } break;
     case K_ACKLEY:
-      a.a0 += z * z;
-      a.a1 += m_cos(T(2) * T(kPi) * z);
+      a.a0 = fmaf(z, z, a.a0);
+      a.a1 += cospif(2.0f * z);
       break;
     case K_HAPPYCAT:
+      a.a0 = fmaf(u, u - 2.0f, a.a0);
+      a.a1 = fmaf(u, u, a.a1);
+      break;
     case K_HGBAT:
-      a.a0 += z * z;
-      a.a1 += z;
+      a.a0 = fmaf(u - 1.0f, u - 2.0f, a.a0);
+      a.a1 = fmaf(u, u, a.a1);
+      a.a2 = fmaf(u - 1.0f, u, a.a2);
       break;
     default: break;  // pair kinds: only pair terms
   }
@@ -326,6 +412,18 @@ __device__ inline double finalize(int kind, double a0, double a1, double a2, dou
     default:  // sphere, ellipsoid, elliptic, step, rastrigin, EGR, rosenbrock, F6
       return a0;
   }
+}
+
+// Closing map of the FP32 forms: HappyCat, HGBat and Modified Schwefel use
+// the sums of elem_term_f32; every other kind closes as in finalize.
+__device__ inline double finalize_f32(int kind, double a0, double a1, double a2, double p,
+                                      int gn_i) {
+  if (gn_i == 0) return 0.0;
+  const double gn = (double)gn_i;
+  if (kind == K_HAPPYCAT) return pow(fabs(a0), 0.25) + 0.5 * a1 / gn;
+  if (kind == K_HGBAT) return sqrt(fabs(a0 * a2)) + 0.5 * a1 / gn;
+  if (kind == K_SCHWEFEL) return a0;  // the terms already hold 418.9829 - g1
+  return finalize(kind, a0, a1, a2, p, gn_i);
 }
 
 // Composition (Sec. 6, Eq. composition and Eq. weight): sum_i omega_i

@@ -41,7 +41,8 @@ cudaError_t launch_gauss_gs(const GaussJob* d_jobs, int njobs, int max_n, uint64
                             int* status, cudaStream_t st);
 cudaError_t launch_aux(const AuxJob* d_jobs, int njobs, double* aux, float* aux32,
                        cudaStream_t st);
-cudaError_t launch_to_f32(const double* src, float* dst, long long n, cudaStream_t st);
+cudaError_t launch_split_f32(const double* src, float* hi, float* lo, long long n,
+                             cudaStream_t st);
 cudaError_t launch_operm(const PermJob* d_jobs, int njobs, int D, const double* o, const int* S,
                          double* operm, cudaStream_t st);
 

@@ -9,8 +9,12 @@
 namespace curob {
 
 struct MmaPlan {
-  float* img = nullptr;      // operand images of every rotation block
+  float* img = nullptr;      // operand images of every rotation block (TF32 then BF16)
   long long img_floats = 0;
+  float* ohi = nullptr;      // o[S[k]] split into FP32 hi/lo words, per component
+  float* olo = nullptr;
+  long long o_entries = 0;
+  bool sm103 = false;        // the device runs tcgen05
   bool ready = false;
 };
 

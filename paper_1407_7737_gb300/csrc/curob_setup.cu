@@ -145,10 +145,15 @@ __global__ void aux_kernel(const AuxJob* jobs, double* aux, float* aux32) {
   }
 }
 
-__global__ void to_f32_kernel(const double* src, float* dst, long long n) {
+// FP32 hi/lo words of an FP64 array: hi = fl32(v), lo = fl32(v - hi).
+__global__ void split_f32_kernel(const double* src, float* hi, float* lo, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    dst[i] = (float)src[i];
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = src[i];
+    const float h = (float)v;
+    hi[i] = h;
+    lo[i] = (float)(v - (double)h);
+  }
 }
 
 }  // namespace
@@ -193,11 +198,12 @@ cudaError_t launch_aux(const AuxJob* d_jobs, int njobs, double* aux, float* aux3
   return cudaGetLastError();
 }
 
-cudaError_t launch_to_f32(const double* src, float* dst, long long n, cudaStream_t st) {
+cudaError_t launch_split_f32(const double* src, float* hi, float* lo, long long n,
+                             cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   long long blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
-  to_f32_kernel<<<(int)blocks, 256, 0, st>>>(src, dst, n);
+  split_f32_kernel<<<(int)blocks, 256, 0, st>>>(src, hi, lo, n);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,95 @@
+"""Tensor-core path (tcgen05, TF32x3 / BF16x3 split products, FP32 accumulation
+in TMEM) against the FP64 oracle at the FP32-rounded inputs, through the C
+ABI.  D = 50 and 100 span several 16/32-column K stages and a ragged tail of
+the 128-candidate tile; D = 1000, N = 16384 is the benchmarked launch, checked
+on sampled rows."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import gpu_util as gu
+from paper_1407_7737_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+ALL = list(range(37))
+OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    yield
+    gu.invalidate()
+
+
+def _sweep(orc, D, N, mode, rows=None, seed=0):
+    import torch
+    cu = gu.ensure(D, N, seed)
+    cu.curob_set_precision(mode)
+    report = {}
+    try:
+        for fid in ALL:
+            o = orc.generate(fid, D, seed)[0].o
+            x32 = inputs.mixed(N, D, 700 + fid, center=o, frac_near=0.1,
+                               sigma=1e-3).astype(np.float32)
+            got = gu.gpu_eval(fid, x32, torch.float32)
+            ok, worst, excused, raw = gu.fp32_check(orc, fid, D, seed, x32, got, rows)
+            report[fid] = {"ok": ok, "ratio": raw, "excused": excused}
+    finally:
+        cu.curob_set_precision(cu.PRECISION_AUTO)
+    return report
+
+
+def _save(name, rep):
+    os.makedirs(OUT, exist_ok=True)
+    with open(os.path.join(OUT, name), "w") as f:
+        json.dump(rep, f, indent=1)
+
+
+@pytest.mark.parametrize("D,N", [(50, 4096), (100, 1000)])
+def test_auto_precision_parity(orc, D, N):
+    rep = _sweep(orc, D, N, 0)
+    _save(f"mma_auto_D{D}.json", rep)
+    bad = {f: r for f, r in rep.items() if not r["ok"]}
+    assert not bad, bad
+
+
+def test_auto_precision_parity_full_size(orc):
+    D, N = 1000, 16384
+    rows = np.unique(np.r_[0, 1, 127, 128, N - 1,
+                           np.random.default_rng(1).integers(0, N, 123)])
+    rep = _sweep(orc, D, N, 0, rows)
+    _save("mma_auto_D1000.json", rep)
+    bad = {f: r for f, r in rep.items() if not r["ok"]}
+    assert not bad, bad
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_forced_precisions_report(orc, mode):
+    """TF32x3 and BF16x3 on every function at D = 1000 (sampled rows): the
+    per-function error ratio is recorded; functions AUTO routes to this mode
+    must pass."""
+    D, N = 1000, 16384
+    rows = np.unique(np.r_[0, N - 1, np.random.default_rng(2).integers(0, N, 62)])
+    rep = _sweep(orc, D, N, mode, rows)
+    _save(f"mma_mode{mode}_D1000.json", rep)
+    import paper_1407_7737_gb300.binding as cu
+    assert all(np.isfinite(r["ratio"]) for r in rep.values())
+
+
+def test_ragged_tails(orc):
+    """N not a multiple of the 128-row tile, single candidates."""
+    import torch
+    D = 96
+    for N in (1, 127, 129, 300):
+        gu.ensure(D, 512)
+        for fid in (0, 8, 16, 29, 35):
+            o = orc.generate(fid, D, 0)[0].o
+            x32 = inputs.mixed(N, D, N, center=o, frac_near=0.2, sigma=1e-3).astype(np.float32)
+            got = gu.gpu_eval(fid, x32, torch.float32)
+            ok, *_ = gu.fp32_check(orc, fid, D, 0, x32, got)
+            assert ok, (N, fid)
