@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="curob", choices=["curob", "reference"])
-    ap.add_argument("--precision", default="auto", choices=["auto", "tf32x3", "bf16x3", "simt"])
+    ap.add_argument("--precision", default="auto",
+                    choices=["auto", "tf32x3", "bf16x3", "simt", "exact"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
@@ -168,21 +169,22 @@ def run_curob(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     cu.curob_initialize(D, N, SEED)
-    mode = {"auto": 0, "tf32x3": 1, "bf16x3": 2, "simt": 3}[args.precision]
+    mode = {"auto": 0, "tf32x3": 1, "bf16x3": 2, "simt": 3, "exact": 4}[args.precision]
     cu.curob_set_precision(mode)
 
-    # 37 FP32 batches, resident in HBM before timing starts
-    X = torch.empty((NFUN, N, D), dtype=torch.float32, device=dev)
+    # 37 FP32 batches, resident in HBM before timing starts (one for a
+    # profiling case)
+    nb = NFUN if args.profile_fid is None else 1
+    X = torch.empty((nb, N, D), dtype=torch.float32, device=dev)
     g = torch.Generator(device=dev)
     g.manual_seed(1234 + rank)
     X.uniform_(-100.0, 100.0, generator=g)
-    OUT = torch.empty((NFUN, N), dtype=torch.float32, device=dev)
+    OUT = torch.empty((nb, N), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     if args.profile_fid is not None:
         for _ in range(2):
-            cu.curob_evaluatef(args.profile_fid, X[args.profile_fid], N, OUT[args.profile_fid],
-                               stream)
+            cu.curob_evaluatef(args.profile_fid, X[0], N, OUT[0], stream)
         torch.cuda.synchronize()
         cu.curob_get_device_status(stream)
         cu.curob_dispose()
@@ -244,7 +246,7 @@ def run_curob(args):
     extra = {}
     fp64 = None
     if rank == 0 and not args.no_extra:
-        for name, m in (("tf32x3", 1), ("bf16x3", 2), ("simt", 3)):
+        for name, m in (("tf32x3", 1), ("bf16x3", 2), ("exact", 4), ("simt", 3)):
             extra[name + "_evals_s"] = round(NFUN * N / (timed_pass(m) / 1e3), 1)
         # FP64 path on the same workload (FP64 copy of the batches)
         x64 = torch.empty((N, D), dtype=torch.float64, device=dev)
@@ -265,7 +267,7 @@ def run_curob(args):
     # roofline of the dominant kernel (the path holding most of the step)
     pk, src = peaks()
     flops = np.array([algorithmic_flops(cu, f) * N for f in range(NFUN)], dtype=np.float64)
-    mma = np.array([m in (1, 2) for m in modes])
+    mma = np.array([m in (1, 2, 4) for m in modes])
     t_mma, t_simt = launch_ms[mma].sum(), launch_ms[~mma].sum()
     if t_mma >= t_simt:
         sel = mma & (flops > 0)
@@ -324,7 +326,7 @@ def run_curob(args):
             "fp64_evals_s": round(fp64, 1) if fp64 else None,
             **extra,
             "per_function_ms": [round(v, 4) for v in launch_ms.tolist()],
-            "per_function_path": ["tf32x3" if m == 1 else "bf16x3" if m == 2 else "simt"
+            "per_function_path": [{1: "tf32x3", 2: "bf16x3", 3: "simt", 4: "exact"}[m]
                                   for m in modes],
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk.summary(), "gpu_launches": gpu_launches,

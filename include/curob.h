@@ -48,15 +48,22 @@ typedef enum {
   CUROB_ERR_UNSUPPORTED = 11         /* size outside what the chosen kernel handles */
 } curob_status;
 
-/* Rotation-contraction precision of curob_evaluatef (north of the paper: the
- * paper evaluates FP32 plainly).  TF32X3: three TF32 tensor-core products per
- * term (hi*hi + hi*lo + lo*hi), FP32 accumulation.  BF16X3: the same with
- * BF16 halves.  SIMT: FP32 CUDA cores.  AUTO (default) picks per function. */
+/* Rotation-contraction precision of curob_evaluatef (the paper evaluates FP32
+ * plainly; these are this library's choices).  TF32X3: three TF32
+ * tensor-core products per term (hi*hi + hi*lo + lo*hi), FP32 accumulation.
+ * BF16X3: the same with BF16 halves.  EXACT: both operands cut into four
+ * 7-bit integer slices held in BF16, accumulated exactly (every partial sum
+ * an integer below 2^24), z to about 2^-28 of each candidate's |x - o|_max.
+ * SIMT: FP32 CUDA cores with a compensated dot product.  AUTO (default):
+ * EXACT for functions containing Discus, Weierstrass, expanded
+ * Griewank-Rosenbrock or Katsuura (they magnify z errors), TF32X3 for the
+ * rest; SIMT where a block is narrower than 16 or wider than 512. */
 typedef enum {
   CUROB_PRECISION_AUTO = 0,
   CUROB_PRECISION_TF32X3 = 1,
   CUROB_PRECISION_BF16X3 = 2,
-  CUROB_PRECISION_SIMT = 3
+  CUROB_PRECISION_SIMT = 3,
+  CUROB_PRECISION_EXACT = 4
 } curob_precision;
 
 /* Number of functions (Table 1). */
@@ -100,7 +107,7 @@ curob_status curob_h_evaluatef(int fid, const float* x, int N, float* out);
 curob_status curob_set_precision(int mode);
 
 /* The precision curob_evaluatef will use for fid under the current setting
- * (AUTO resolved): CUROB_PRECISION_TF32X3, _BF16X3 or _SIMT.  Host pointer.
+ * (AUTO resolved): CUROB_PRECISION_TF32X3, _BF16X3, _EXACT or _SIMT.
  * Errors: NOT_INITIALIZED, INVALID_FID, INVALID_DIM, NULL_POINTER,
  * UNSUPPORTED (a forced tensor-core precision the instance cannot use). */
 curob_status curob_query_precision(int fid, int* mode);

@@ -20,7 +20,7 @@ STATUS = {
 }
 CODES = {v: k for k, v in STATUS.items()}
 
-PRECISION_AUTO, PRECISION_TF32X3, PRECISION_BF16X3, PRECISION_SIMT = 0, 1, 2, 3
+PRECISION_AUTO, PRECISION_TF32X3, PRECISION_BF16X3, PRECISION_SIMT, PRECISION_EXACT = 0, 1, 2, 3, 4
 NUM_FUNCTIONS = 37
 FOPT = 100.0
 

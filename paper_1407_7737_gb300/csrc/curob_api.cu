@@ -384,7 +384,9 @@ bool device_accessible(const void* p) {
 int resolve_precision(const Function& F) {
   int mode = g.precision;
   const bool mma_ok = mma_supports(g.mma, F);
-  if ((mode == CUROB_PRECISION_TF32X3 || mode == CUROB_PRECISION_BF16X3) && !mma_ok) return -1;
+  const bool tc = mode == CUROB_PRECISION_TF32X3 || mode == CUROB_PRECISION_BF16X3 ||
+                  mode == CUROB_PRECISION_EXACT;
+  if (tc && !mma_ok) return -1;
   if (mode == CUROB_PRECISION_AUTO) mode = mma_ok ? mma_auto_mode(g.mma, F) : CUROB_PRECISION_SIMT;
   return mode;
 }
@@ -506,8 +508,7 @@ curob_status curob_evaluatef(int fid, const float* x, int N, float* out, curob_s
   if (mode == CUROB_PRECISION_SIMT)
     e = launch_simt_f32(tables(), F, x, N, out, (cudaStream_t)stream);
   else
-    e = launch_mma(g.mma, tables(), F, mode == CUROB_PRECISION_BF16X3, x, N, out,
-                   (cudaStream_t)stream);
+    e = launch_mma(g.mma, tables(), F, mode, x, N, out, (cudaStream_t)stream);
   return e == cudaSuccess ? CUROB_OK : CUROB_ERR_CUDA;
 }
 
@@ -542,7 +543,7 @@ curob_status curob_h_evaluatef(int fid, const float* x, int N, float* out) {
 }
 
 curob_status curob_set_precision(int mode) {
-  if (mode < CUROB_PRECISION_AUTO || mode > CUROB_PRECISION_SIMT)
+  if (mode < CUROB_PRECISION_AUTO || mode > CUROB_PRECISION_EXACT)
     return CUROB_ERR_INVALID_ARGUMENT;
   g.precision = mode;
   return CUROB_OK;

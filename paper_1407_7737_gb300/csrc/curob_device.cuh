@@ -42,6 +42,7 @@ struct Segment {
   long long r_off;    // rotation block (n x n, row-major) in the rotation pools
   long long aux_off;  // per-variable table of the block (n entries)
   long long img_off;  // tensor-core operand image of R_b (floats)
+  long long tau_off;  // row scales of R_b's integer slices (tensor-core EXACT)
   int npad;           // n rounded up to the tensor-core tile
   int comp;           // owning component (index into the component table)
 };

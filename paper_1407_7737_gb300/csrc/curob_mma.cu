@@ -2,31 +2,46 @@
 //
 // The block rotation z_b = R_b y_b of the General Setup is a dense
 // contraction per block: for a tile of 128 candidates, Z_b (128 x n_b) =
-// Y_b (128 x n_b) R_b^T.  It runs on tcgen05 in split precision:
-//   TF32X3: y = yh + yl, R = Rh + Rl (TF32 halves), Z = Yh Rh + Yh Rl + Yl Rh
-//   BF16X3: the same with BF16 halves,
-// accumulated in FP32 in tensor memory (TMEM), then transformed and reduced
-// by the epilogue warps straight out of TMEM.
+// Y_b (128 x n_b) R_b^T, run on tcgen05 with the accumulators in tensor
+// memory (TMEM), then transformed and reduced by the epilogue warps straight
+// out of TMEM.  Three precisions:
+//   TF32X3  y = yh + yl, R = Rh + Rl (TF32 halves), Z = Yh Rh + Yh Rl + Yl Rh,
+//           one FP32 accumulator;
+//   BF16X3  the same with BF16 halves;
+//   EXACT   y / sigma_m and R / tau_i (powers of two) cut into four 7-bit
+//           integer slices each, held exactly in BF16; the ten slice products
+//           of weight 2^-7(a+b), a + b <= 5, accumulate in four accumulators,
+//           one per weight.  Every partial sum is an integer below 2^24, so
+//           the FP32 accumulation is exact whatever the tensor core's
+//           rounding; z = sigma tau sum_g 2^-7g P_g to about 2^-28 of the row
+//           scale.  (The error-free splitting of matrix products of Ozaki,
+//           Ogita, Oishi and Rump, with BF16 integer slices.)
+// The tensor core's FP32 accumulation truncates: over a 334-long block TF32X3
+// loses ~2e-6 of |z| systematically, which the functions that magnify z
+// errors (Discus, Weierstrass, Griewank-Rosenbrock, Katsuura) cannot absorb;
+// they take EXACT.
 //
 // Warp roles of one CTA (one tile of 128 candidates, 1 CTA per SM):
-//   warps 0-3  producers: gather x at the block's variables (S_b), take the
-//              shift y = x - o in double-float (exact TwoSum, then the low
-//              word of o), split y into hi/lo and store the A operand in the
-//              64-byte-swizzled K-major layout the tensor core reads;
-//   warps 4-7  epilogue: thread t owns candidate row t (TMEM lane t), loads
-//              its z row 32 columns at a time (tcgen05.ld), applies
-//              z = s z + c, the per-variable transform and the running sums
-//              (FP32 per 32 columns, FP64 across), closes functions, mixes
-//              composition members (FP64) and writes f;
-//   warp 8     allocates TMEM and issues the MMAs (one elected lane);
-//   warp 9     loads the B operand (R_b hi/lo, pre-laid-out in global memory
-//              in exactly the shared-memory image) with one bulk copy per
-//              stage (cp.async.bulk, the TMA engine).
-// Stages of K (16 TF32 or 32 BF16 columns = 64 bytes per row) rotate through
-// shared memory under full/empty mbarriers; the accumulator is handed from
-// the MMA warp to the epilogue and back under tmem_full/tmem_empty.  Every
-// wait is bounded: past ~2 s it raises DEV_TIMEOUT in the status word, the
-// CTA stops, and TMEM is freed before exit.
+//   warps 0-3  producers: thread = candidate row.  Per block the block's
+//              index list and o hi/lo words are staged in shared memory; per
+//              K stage a thread gathers its row's x at the block's variables
+//              (prefetching the next stage's values), takes y = x - o in
+//              double-float (exact TwoSum, then o's low word), splits or
+//              slices it and stores its 64-byte rows of the A operand in the
+//              64-byte-swizzled K-major layout; it also sums ||x - o||^2.
+//   warps 4-7  epilogue: thread t owns row t (TMEM lane t), loads its z
+//              32 columns at a time (tcgen05.ld), applies z = s z + c, the
+//              per-variable transform and the running sums (FP32 per 32
+//              columns, FP64 across), closes functions.
+//   warp 8     allocates TMEM and issues the MMAs (one lane).
+//   warp 9     loads the B operand (R_b parts, pre-laid-out in global memory
+//              as the exact shared-memory image) with one bulk copy per stage
+//              (cp.async.bulk, the TMA engine).
+// Stages rotate through shared memory under full/empty mbarriers; the
+// accumulators are handed from the MMA warp to the epilogue and back under
+// tmem_full/tmem_empty.  Every wait is bounded: past ~2 s it raises
+// DEV_TIMEOUT in the status word, the CTA stops, and TMEM is freed before
+// exit.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -38,10 +53,14 @@ namespace {
 
 constexpr int kTileM = 128;
 constexpr int kThreads = 320;
-constexpr int kRowBytes = 64;                 // one K-stage row: 64 B (SW64)
-constexpr int kATileBytes = kTileM * kRowBytes;  // 8 KB per hi/lo
+constexpr int kRowBytes = 64;                    // one K-stage row: 64 B (SW64)
+constexpr int kPartBytes = kTileM * kRowBytes;   // 8 KB per A part
 constexpr unsigned long long kTimeoutNs = 2000000000ull;
-constexpr int kMaxNpad = 512;                 // TMEM columns
+constexpr int kMaxNpad = 512;                    // TMEM columns
+constexpr int kExactNC = 128;                    // EXACT: N chunk (4 groups x 128)
+constexpr int kSigRing = 8;                      // EXACT: row scales in flight
+
+enum Mode : int { M_TF32 = 0, M_BF16 = 1, M_EXACT = 2 };
 
 // -------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -99,6 +118,16 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
+// Barrier of the 4 producer warps on an mbarrier (count 4), bounded like
+// every other wait; `phase` counts its uses.
+__device__ __forceinline__ bool producers_sync(uint64_t* bar, uint32_t& phase,
+                                               volatile int* abort_flag, int* status) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
+  const bool ok = mbar_wait(bar, phase & 1u, abort_flag, status);
+  ++phase;
+  return ok;
+}
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -112,18 +141,18 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
           smem_u32(bar))
       : "memory");
 }
-template <bool kBf16>
+template <bool kTf32>
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                        uint32_t accumulate) {
-  if constexpr (kBf16) {
+  if constexpr (kTf32) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
   } else {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
   }
 }
@@ -151,10 +180,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 __device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1u << 16;                     // LBO (unused for swizzled K-major)
+  d |= (uint64_t)1u << 16;                       // LBO (unused for swizzled K-major)
   d |= (uint64_t)((512u >> 4) & 0x3FFFu) << 32;  // SBO
-  d |= (uint64_t)1u << 46;                     // version
-  d |= (uint64_t)4u << 61;                     // SWIZZLE_64B
+  d |= (uint64_t)1u << 46;                       // version
+  d |= (uint64_t)4u << 61;                       // SWIZZLE_64B
   return d;
 }
 // Instruction descriptor: FP32 accumulator, A/B format (TF32 = 2, BF16 = 1),
@@ -163,8 +192,8 @@ __host__ __device__ constexpr uint32_t idesc_make(uint32_t fmt, uint32_t M, uint
   return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
-// Byte offset of element (row, byte-in-row) in the 64-byte-swizzled image:
-// the 16-byte chunk index (bits 4-5) XOR bits 7-8 of the linear offset.
+// Byte offset of (row, byte-in-row) in the 64-byte-swizzled image: the
+// 16-byte chunk index (bits 4-5) XOR bits 7-8 of the linear offset.
 __host__ __device__ __forceinline__ uint32_t swz64(uint32_t row, uint32_t byte_in_row) {
   uint32_t off = row * kRowBytes + byte_in_row;
   return off ^ (((off >> 7) & 3u) << 4);
@@ -175,14 +204,30 @@ __device__ __forceinline__ uint32_t to_tf32(float v) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
   return r;
 }
-
-// x - o with o = ohi + olo: TwoSum(x, -ohi) is exact, the low word follows.
-__device__ __forceinline__ float shift_ff(float x, float ohi, float olo) {
-  float s = __fsub_rn(x, ohi);
-  float bb = __fsub_rn(s, x);
-  float err = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bb)), __fsub_rn(-ohi, bb));
-  return __fadd_rn(s, __fsub_rn(err, olo));
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
 }
+
+// x - o with o = ohi + olo as a double-float (yh, yl): TwoSum(x, -ohi) is
+// exact, then the low word of o.
+__device__ __forceinline__ void shift_ff(float x, float ohi, float olo, float& yh, float& yl) {
+  const float s = __fsub_rn(x, ohi);
+  const float bb = __fsub_rn(s, x);
+  const float err = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bb)), __fsub_rn(-ohi, bb));
+  const float t = __fsub_rn(err, olo);
+  yh = __fadd_rn(s, t);
+  yl = __fsub_rn(t, __fsub_rn(yh, s));
+}
+
+// Mode constants.
+template <int kMode> struct MC {
+  static constexpr int kParts = kMode == M_EXACT ? 4 : 2;  // A/B operand parts
+  static constexpr int kKs = kMode == M_TF32 ? 16 : 32;    // K columns per stage
+  static constexpr int kEl = kMode == M_TF32 ? 4 : 2;      // bytes per element
+  static constexpr int kMmaK = kMode == M_TF32 ? 8 : 16;   // K per MMA
+  static constexpr uint32_t kFmt = kMode == M_TF32 ? 2u : 1u;
+};
 
 struct MmaArgs {
   Tables tb;
@@ -192,23 +237,126 @@ struct MmaArgs {
   int N;
   const float* ohi;      // o[S[k]] high words per component
   const float* olo;      // low words
-  const uint8_t* img;    // B images (TF32 or BF16 pool)
+  const uint8_t* img;    // operand images
+  const float* tau;      // EXACT: row scales of R (powers of two)
+  const float* onat;     // EXACT: o per component in natural order, FP32
   int nstage;
-  int stage_bytes;       // A hi + A lo + B hi + B lo
-  int b_bytes_max;
+  int stage_bytes;
 };
 
+// Floats reserved per block for each precision's image (the TF32 size; BF16
+// needs half).  A block's images: [TF32][BF16][EXACT].
+__host__ __device__ inline long long image_floats(int npad) { return 2LL * npad * npad; }
+
+// ------------------------------------------------------- epilogue helpers
+// Running state of the open basic function of one candidate row.
+struct EpiState {
+  double a0 = 0, a1 = 0, a2 = 0, p = 1;
+  float zfirst = 0.f, zprev = 0.f;
+  __device__ void open() {
+    a0 = a1 = a2 = 0.0;
+    p = 1.0;
+  }
+  // closes the function (cyclic pair, closing map); value without f_opt
+  __device__ double close(int kind, int gn) {
+    if (kind_is_cyclic(kind)) a0 += (double)pair_term<float>(kind, zprev, zfirst);
+    return finalize_f32(kind, a0, a1, a2, p, gn);
+  }
+};
+struct EpiSeg {
+  float s, c0, gnT, kat_e;
+  const float* aux;
+  int gpos, gfirst;
+};
+
+// Kinds whose per-variable term calls transcendentals with slow paths (large
+// arguments): their term is one out-of-line call, so the unrolled chunk loop
+// stays small; contributions come back by value (no local memory).
+__host__ __device__ constexpr bool kind_is_heavy(int k) {
+  return k == K_POWERS || k == K_WEIERSTRASS || k == K_GRIEWANK || k == K_SCHAFFER7 ||
+         k == K_EGR || k == K_SCHWEFEL || k == K_KATSUURA || k == K_SCHAFFER6;
+}
+__device__ __noinline__ float4 heavy_term(int kind, float z, float u, int gi, float gn, float aux,
+                                          float kat_e) {
+  Acc<float> a = acc_zero<float>();
+  elem_term_f32(kind, z, u, gi, gn, aux, kat_e, a);
+  return make_float4(a.a0, a.a1, a.a2, a.p);
+}
+__device__ __noinline__ float heavy_pair(int kind, float zp, float z) {
+  return pair_term<float>(kind, zp, z);
+}
+
+// 32 accumulator columns [c, c + cend) of one row, for a fixed kind: the
+// loop is unrolled so the values stay in registers.
+template <int KIND>
+__device__ __forceinline__ void epi_chunk_k(const float* v, int c, int cend, const EpiSeg& es,
+                                            EpiState& st) {
+  constexpr bool kPairs = (KIND == K_SCHAFFER7 || KIND == K_EGR || KIND == K_ROSENBROCK ||
+                           KIND == K_SCHAFFER6);
+  constexpr bool kAux = (KIND == K_ELLIPTIC || KIND == K_POWERS || KIND == K_GRIEWANK);
+  Acc<float> part = acc_zero<float>();
+  float zprev = st.zprev;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    if (k < cend) {
+      const int col = c + k;
+      const float u = v[k] * es.s;  // z before its offset
+      const float z = u + es.c0;
+      if constexpr (kind_is_heavy(KIND)) {
+        if (KIND != K_SCHAFFER7 && KIND != K_EGR && KIND != K_SCHAFFER6) {
+          const float4 t = heavy_term(KIND, z, u, es.gpos + col, es.gnT,
+                                      kAux ? es.aux[col] : 0.f, es.kat_e);
+          part.a0 += t.x;
+          part.a1 += t.y;
+          part.a2 += t.z;
+          part.p *= t.w;
+        }
+      } else {
+        elem_term_f32(KIND, z, u, es.gpos + col, es.gnT, kAux ? es.aux[col] : 0.f, es.kat_e,
+                      part);
+      }
+      if (kPairs) {
+        if (col == 0 && es.gfirst) st.zfirst = z;
+        else if (kind_is_heavy(KIND)) part.a0 += heavy_pair(KIND, zprev, z);
+        else part.a0 += pair_term<float>(KIND, zprev, z);
+      } else if (col == 0 && es.gfirst) {
+        st.zfirst = z;
+      }
+      zprev = z;
+    }
+  }
+  st.zprev = zprev;
+  st.a0 += (double)part.a0;
+  st.a1 += (double)part.a1;
+  st.a2 += (double)part.a2;
+  st.p *= (double)part.p;
+}
+
+__device__ __forceinline__ void epi_chunk(int kind, const float* v, int c, int cend,
+                                          const EpiSeg& es, EpiState& st) {
+  switch (kind) {
+#define CUROB_EPI_CASE(K) \
+  case K: epi_chunk_k<K>(v, c, cend, es, st); break;
+    CUROB_EPI_CASE(K_SPHERE) CUROB_EPI_CASE(K_ELLIPSOID) CUROB_EPI_CASE(K_ELLIPTIC)
+    CUROB_EPI_CASE(K_DISCUS) CUROB_EPI_CASE(K_CIGAR) CUROB_EPI_CASE(K_POWERS)
+    CUROB_EPI_CASE(K_SHARPV) CUROB_EPI_CASE(K_STEP) CUROB_EPI_CASE(K_WEIERSTRASS)
+    CUROB_EPI_CASE(K_GRIEWANK) CUROB_EPI_CASE(K_RASTRIGIN) CUROB_EPI_CASE(K_SCHAFFER7)
+    CUROB_EPI_CASE(K_EGR) CUROB_EPI_CASE(K_ROSENBROCK) CUROB_EPI_CASE(K_SCHWEFEL)
+    CUROB_EPI_CASE(K_KATSUURA) CUROB_EPI_CASE(K_LUNACEK) CUROB_EPI_CASE(K_ACKLEY)
+    CUROB_EPI_CASE(K_HAPPYCAT) CUROB_EPI_CASE(K_HGBAT) CUROB_EPI_CASE(K_SCHAFFER6)
+#undef CUROB_EPI_CASE
+    default: break;
+  }
+}
+
 // -------------------------------------------------------------- the kernel
-template <bool kBf16>
+template <int kMode>
 __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
-  constexpr int kKs = kBf16 ? 32 : 16;          // K columns per stage
-  constexpr int kEl = kBf16 ? 2 : 4;            // bytes per element
-  constexpr int kMmaK = kBf16 ? 16 : 8;         // K per MMA instruction
-  constexpr int kKsteps = kKs / kMmaK;          // 2
-  constexpr uint32_t kFmt = kBf16 ? 1u : 2u;
+  using C = MC<kMode>;
+  constexpr int kKs = C::kKs, kEl = C::kEl, kParts = C::kParts;
+  constexpr int kKsteps = kKs / C::kMmaK;
 
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  // stage bases must sit on 1024-byte boundaries (swizzle atoms)
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const Tables& tb = args.tb;
   const Function& F = args.F;
@@ -221,10 +369,17 @@ __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
   uint64_t* empty = full + args.nstage;
   uint64_t* tmem_full = empty + args.nstage;
   uint64_t* tmem_empty = tmem_full + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_empty + 1);
+  uint64_t* sig_full = tmem_empty + 1;                       // [kSigRing]
+  uint64_t* prod_bar = sig_full + kSigRing;
+  uint64_t* gbar = prod_bar + 1;                             // [nstage] gathers landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbar + args.nstage);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  double* rowG = reinterpret_cast<double*>(ctrl + 256);        // [kMaxComponents][128]
+  double* rowG = reinterpret_cast<double*>(ctrl + 256);       // [kMaxComponents][128]
   double* rowD2 = rowG + kMaxComponents * kTileM;             // [kMaxComponents][128]
+  float* rowSig = reinterpret_cast<float*>(rowD2 + kMaxComponents * kTileM);  // [kSigRing][128]
+  int* tabS = reinterpret_cast<int*>(rowSig + kSigRing * kTileM);             // [kMaxNpad]
+  float* tabH = reinterpret_cast<float*>(tabS + kMaxNpad);
+  float* tabL = tabH + kMaxNpad;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < args.nstage; ++s) {
@@ -232,7 +387,10 @@ __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
       mbar_init(&empty[s], 1);  // one tcgen05.commit
     }
     mbar_init(tmem_full, 1);
-    mbar_init(tmem_empty, 4);  // the 4 epilogue warps
+    mbar_init(tmem_empty, 4);   // the 4 epilogue warps
+    for (int s = 0; s < kSigRing; ++s) mbar_init(&sig_full[s], 4);
+    mbar_init(prod_bar, 4);     // the 4 producer warps
+    for (int s = 0; s < args.nstage; ++s) mbar_init(&gbar[s], 128);  // producer threads' cp.async
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -251,78 +409,196 @@ __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
 
   if (warp < 4) {
     // ------------------------------------------------------------ producers
-    // thread = candidate row r of the tile: per stage it gathers its row's
-    // kKs variables, shifts, splits and stores one 64-byte row of A_hi/A_lo;
-    // it also sums ||x - o||^2 of its row for the composition weights.
+    // Thread = candidate row r.  The raw x values of a K stage are gathered
+    // with 4-byte cp.async straight into the stage's own A area (row r only:
+    // the first 64 bytes of part 0's row r, then part 1's), nstage - 1 stages
+    // ahead; converting a stage reads the thread's own raw row back, then
+    // overwrites that row of every part, so no other thread is involved.
     const int r = warp * 32 + lane;
     const long long grow = row0 + r;
     const bool vrow = grow < args.N;
     const float* xrow = args.x + (vrow ? grow : 0) * (long long)D;
-    uint32_t it = 0;
-    for (int ci = 0; ci < F.ncomp && !*abort_flag; ++ci) {
-      const Component C = tb.comp[F.comp0 + ci];
-      const int* S = tb.S + C.base;
-      const float* ohi = args.ohi + C.base;
-      const float* olo = args.olo + C.base;
+    const int P = args.nstage - 1;  // gather prefetch depth (stages)
+    uint32_t it = 0, pphase = 0;
+    bool ok = true;
+    for (int ci = 0; ci < F.ncomp && ok; ++ci) {
+      const Component Cm = tb.comp[F.comp0 + ci];
+      const int* S = tb.S + Cm.base;
+      const float* ohi = args.ohi + Cm.base;
+      const float* olo = args.olo + Cm.base;
       double d2 = 0.0;
-      for (int si = 0; si < C.nseg && !*abort_flag; ++si) {
-        const Segment sg = tb.seg[C.seg0 + si];
-        const int nslab = (sg.npad + kKs - 1) / kKs;
-        const int* Sb = S + sg.zoff;
-        const float* oh = ohi + sg.zoff;
-        const float* ol = olo + sg.zoff;
-        for (int t = 0; t < nslab; ++t, ++it) {
-          const int stage = it % args.nstage;
-          const uint32_t ph = (it / args.nstage) & 1u;
-          if (!mbar_wait(&empty[stage], ph ^ 1u, abort_flag, tb.status)) break;
-          uint8_t* A_hi = stages + (size_t)stage * args.stage_bytes;
-          uint8_t* A_lo = A_hi + kATileBytes;
-          float y[kKs];
-#pragma unroll
-          for (int k = 0; k < kKs; ++k) {
-            const int j = t * kKs + k;
-            y[k] = 0.f;
-            if (j < sg.n && vrow) y[k] = shift_ff(__ldg(xrow + Sb[j]), oh[j], ol[j]);
+      float isig = 1.f;
+      if constexpr (kMode == M_EXACT) {
+        // row scale sigma_m = 2^e > max_j |x_j - o_j| over the component,
+        // read in natural order (contiguous row, o as FP32)
+        float mx = 0.f;
+        if (vrow) {
+          const float* on = args.onat + Cm.base;
+          int k = 0;
+          if ((D & 3) == 0) {
+            const float4* x4 = reinterpret_cast<const float4*>(xrow);
+            const float4* o4 = reinterpret_cast<const float4*>(on);
+#pragma unroll 4
+            for (; k < D / 4; ++k) {
+              const float4 a = __ldg(x4 + k), b = __ldg(o4 + k);
+              mx = fmaxf(mx, fmaxf(fmaxf(fabsf(a.x - b.x), fabsf(a.y - b.y)),
+                                   fmaxf(fabsf(a.z - b.z), fabsf(a.w - b.w))));
+            }
+            k *= 4;
           }
-          float d2p = 0.f;
+          for (; k < D; ++k) mx = fmaxf(mx, fabsf(__ldg(xrow + k) - on[k]));
+        }
+        int e = 0;
+        if (mx > 0.f && mx < 3.0e38f) e = ilogbf(mx * 1.0009765625f) + 1;
+        isig = ldexpf(1.f, -e);
+        rowSig[(ci % kSigRing) * kTileM + r] = ldexpf(1.f, e);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sig_full[ci % kSigRing]);
+      }
+      for (int si = 0; si < Cm.nseg && ok; ++si) {
+        const Segment sg = tb.seg[Cm.seg0 + si];
+        // stage the block's index list and o words in shared memory (the
+        // previous block's readers are done at the first barrier)
+        if (!producers_sync(prod_bar, pphase, abort_flag, tb.status)) { ok = false; break; }
+        for (int k = r; k < sg.npad; k += kTileM) {
+          const bool in = k < sg.n;
+          tabS[k] = in ? S[sg.zoff + k] : 0;
+          tabH[k] = in ? ohi[sg.zoff + k] : 0.f;
+          tabL[k] = in ? olo[sg.zoff + k] : 0.f;
+        }
+        if (!producers_sync(prod_bar, pphase, abort_flag, tb.status)) { ok = false; break; }
+        const int nslab = sg.npad / kKs;
+        const int nchunk = kMode == M_EXACT ? (sg.npad + kExactNC - 1) / kExactNC : 1;
+        const int total = nslab * nchunk;  // stages of this block
+        const uint32_t it0 = it;
+        // raw x of stage q, row rr: kKs floats at part 0 row rr (first 16)
+        // and part 1 row rr (next 16).  Lanes walk a row's (sorted) columns,
+        // so one instruction touches one or two rows' few sectors; each
+        // thread's copies arrive on gbar[stage] when they land.
+        auto issue = [&](int q) -> bool {
+          const uint32_t g = it0 + (uint32_t)q;
+          const int stage = g % args.nstage;
+          if (!mbar_wait(&empty[stage], ((g / args.nstage) & 1u) ^ 1u, abort_flag, tb.status))
+            return false;
+          uint8_t* A = stages + (size_t)stage * args.stage_bytes;
+          const int t = q % nslab;
+          constexpr int kRowsPerInst = 32 / kKs;            // 2 (TF32) or 1
+          const int k = lane % kKs;                         // column of the stage
+          const int j = t * kKs + k;
+          const bool cin = j < sg.n;
+          const int col = cin ? tabS[j] : 0;
+          const uint32_t dcol = (uint32_t)((k >> 4) * kPartBytes + (k & 15) * 4);
+#pragma unroll 4
+          for (int i = 0; i < 32 / kRowsPerInst; ++i) {
+            const int rr = warp * 32 + i * kRowsPerInst + lane / kKs;
+            const long long gr = row0 + rr;
+            const bool in = cin && gr < args.N;
+            const float* src = in ? args.x + gr * (long long)D + col : args.x;
+            const uint32_t dst = smem_u32(A + rr * kRowBytes) + dcol;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src),
+                         "r"(in ? 4 : 0)
+                         : "memory");
+          }
+          asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
+                           smem_u32(&gbar[stage]))
+                       : "memory");
+          return true;
+        };
+        const int npre = min(P, total);
+        for (int q = 0; q < npre && ok; ++q) ok = issue(q);
+        for (int q = 0; q < total && ok; ++q, ++it) {
+          if (!mbar_wait(&gbar[it % args.nstage], (it / args.nstage) & 1u, abort_flag, tb.status)) {
+            ok = false;
+            break;
+          }
+          const int stage = it % args.nstage;
+          uint8_t* A = stages + (size_t)stage * args.stage_bytes;
+          const int t = q % nslab;
+          float yh[kKs], yl[kKs];
 #pragma unroll
-          for (int k = 0; k < kKs; ++k) d2p = fmaf(y[k], y[k], d2p);
-          d2 += (double)d2p;
-          // one 64-byte row = four 16-byte chunks, each stored whole
+          for (int k = 0; k < kKs; k += 4) {
+            const float4 xv = *reinterpret_cast<const float4*>(
+                A + (k >> 4) * kPartBytes + r * kRowBytes + (k & 15) * 4);
+            const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int j = t * kKs + k + u;
+              if (vrow && j < sg.n) {
+                shift_ff(xs[u], tabH[j], tabL[j], yh[k + u], yl[k + u]);
+              } else {
+                yh[k + u] = 0.f;
+                yl[k + u] = 0.f;
+              }
+            }
+          }
+          if (q < nslab) {  // first chunk: ||x - o||^2 of the row
+            float d2p = 0.f;
+#pragma unroll
+            for (int k = 0; k < kKs; ++k) d2p = fmaf(yh[k], yh[k], d2p);
+            d2 += (double)d2p;
+          }
+          // one 64-byte row per part = four 16-byte chunks, each stored whole
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             const uint32_t off = swz64((uint32_t)r, (uint32_t)(c * 16));
-            uint4 h, l;
-            if constexpr (kBf16) {
+            if constexpr (kMode == M_TF32) {
               uint32_t hw[4], lw[4];
 #pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const float a = y[c * 8 + 2 * q], b = y[c * 8 + 2 * q + 1];
-                __nv_bfloat162 hh = __floats2bfloat162_rn(a, b);
-                const float2 hf = __bfloat1622float2(hh);
-                __nv_bfloat162 ll = __floats2bfloat162_rn(a - hf.x, b - hf.y);
-                hw[q] = *reinterpret_cast<uint32_t*>(&hh);
-                lw[q] = *reinterpret_cast<uint32_t*>(&ll);
+              for (int qq = 0; qq < 4; ++qq) {
+                const float a = yh[c * 4 + qq];
+                hw[qq] = to_tf32(a);
+                lw[qq] = to_tf32((a - __uint_as_float(hw[qq])) + yl[c * 4 + qq]);
               }
-              h = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-              l = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+              *reinterpret_cast<uint4*>(A + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+              *reinterpret_cast<uint4*>(A + kPartBytes + off) =
+                  make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            } else if constexpr (kMode == M_BF16) {
+              uint32_t hw[4], lw[4];
+#pragma unroll
+              for (int qq = 0; qq < 4; ++qq) {
+                const float a = yh[c * 8 + 2 * qq], b = yh[c * 8 + 2 * qq + 1];
+                hw[qq] = pack_bf16(a, b);
+                const float2 hf = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&hw[qq]));
+                lw[qq] = pack_bf16((a - hf.x) + yl[c * 8 + 2 * qq],
+                                   (b - hf.y) + yl[c * 8 + 2 * qq + 1]);
+              }
+              *reinterpret_cast<uint4*>(A + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+              *reinterpret_cast<uint4*>(A + kPartBytes + off) =
+                  make_uint4(lw[0], lw[1], lw[2], lw[3]);
             } else {
-              uint32_t hw[4], lw[4];
+              // four 7-bit integer slices of y / sigma (exact in BF16)
+              uint32_t w[4][4];
 #pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const float a = y[c * 4 + q];
-                hw[q] = to_tf32(a);
-                lw[q] = to_tf32(a - __uint_as_float(hw[q]));
+              for (int qq = 0; qq < 4; ++qq) {
+                float sl[2][4];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                  const int k = c * 8 + 2 * qq + e;
+                  const float v = yh[k] * isig * 128.f;
+                  const float y1 = rintf(v);
+                  const float v2 = ((v - y1) + yl[k] * isig * 128.f) * 128.f;
+                  const float y2 = rintf(v2);
+                  const float v3 = (v2 - y2) * 128.f;
+                  const float y3 = rintf(v3);
+                  const float y4 = rintf((v3 - y3) * 128.f);
+                  sl[e][0] = y1;
+                  sl[e][1] = y2;
+                  sl[e][2] = y3;
+                  sl[e][3] = y4;
+                }
+#pragma unroll
+                for (int pp = 0; pp < 4; ++pp) w[pp][qq] = pack_bf16(sl[0][pp], sl[1][pp]);
               }
-              h = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-              l = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+#pragma unroll
+              for (int pp = 0; pp < 4; ++pp)
+                *reinterpret_cast<uint4*>(A + pp * kPartBytes + off) =
+                    make_uint4(w[pp][0], w[pp][1], w[pp][2], w[pp][3]);
             }
-            *reinterpret_cast<uint4*>(A_hi + off) = h;
-            *reinterpret_cast<uint4*>(A_lo + off) = l;
           }
           fence_proxy_async();
           __syncwarp();
           if (lane == 0) mbar_arrive(&full[stage]);
+          if (q + P < total) ok = issue(q + P);
         }
       }
       rowD2[ci * kTileM + r] = d2;
@@ -332,103 +608,137 @@ __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
     const int q = warp - 4;                 // TMEM lane quadrant
     const int r = q * 32 + lane;            // candidate row in the tile
     const uint32_t t_lane = tmem_base + ((uint32_t)(q * 32) << 16);
-    uint32_t seg_it = 0;
-    double a0 = 0, a1 = 0, a2 = 0, p = 1, gsum = 0;
-    float zfirst = 0.f, zprev = 0.f;
+    uint32_t chunk_it = 0;
+    EpiState st;
     for (int ci = 0; ci < F.ncomp && !*abort_flag; ++ci) {
-      const Component C = tb.comp[F.comp0 + ci];
-      gsum = 0.0;
-      for (int si = 0; si < C.nseg; ++si, ++seg_it) {
-        const Segment sg = tb.seg[C.seg0 + si];
-        if (!mbar_wait(tmem_full, seg_it & 1u, abort_flag, tb.status)) break;
-        tc_fence_after();
-        const int kind = sg.kind;
-        const bool pairs = kind_has_pairs(kind);
-        const float s = (float)sg.scale, c0 = (float)sg.offset, gnT = (float)sg.gn;
-        const float kat_e = (kind == K_KATSUURA) ? (float)(10.0 / pow((double)sg.gn, 1.2)) : 0.f;
-        const float* aux = tb.aux32 + (sg.aux_off >= 0 ? sg.aux_off : 0);
-        const bool has_aux = sg.aux_off >= 0;
-        if (sg.gfirst) {
-          a0 = a1 = a2 = 0.0;
-          p = 1.0;
-        }
-        for (int c = 0; c < sg.n; c += 32) {
-          float v[32];
-          tmem_ld32(t_lane + (uint32_t)c, v);
-          Acc<float> part = acc_zero<float>();
-          const int cend = min(32, sg.n - c);
-          for (int k = 0; k < cend; ++k) {
-            const float acc = v[k];
-            const float u = acc * s;       // z before its offset
-            const float z = u + c0;
-            const int col = c + k;
-            elem_term_f32(kind, z, u, sg.gpos + col, gnT, has_aux ? aux[col] : 0.f, kat_e, part);
-            if (col == 0 && sg.gfirst) {
-              zfirst = z;
-            } else if (pairs) {
-              part.a0 += pair_term<float>(kind, zprev, z);
-            }
-            zprev = z;
-          }
-          a0 += (double)part.a0;
-          a1 += (double)part.a1;
-          a2 += (double)part.a2;
-          p *= (double)part.p;
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(tmem_empty);
-        if (sg.glast) {
-          if (kind_is_cyclic(kind)) a0 += (double)pair_term<float>(kind, zprev, zfirst);
-          gsum += finalize_f32(kind, a0, a1, a2, p, sg.gn);
-        }
+      const Component Cm = tb.comp[F.comp0 + ci];
+      double gsum = 0.0;
+      float sig = 1.f;
+      if constexpr (kMode == M_EXACT) {
+        if (!mbar_wait(&sig_full[ci % kSigRing], (ci / kSigRing) & 1u, abort_flag, tb.status))
+          break;
+        sig = rowSig[(ci % kSigRing) * kTileM + r];
       }
+      bool ok = true;
+      for (int si = 0; si < Cm.nseg && ok; ++si) {
+        const Segment sg = tb.seg[Cm.seg0 + si];
+        const int kind = sg.kind;
+        EpiSeg es;
+        es.s = (float)sg.scale;
+        es.c0 = (float)sg.offset;
+        es.gnT = (float)sg.gn;
+        es.kat_e = (kind == K_KATSUURA) ? (float)(10.0 / pow((double)sg.gn, 1.2)) : 0.f;
+        es.aux = sg.aux_off >= 0 ? tb.aux32 + sg.aux_off : nullptr;
+        es.gpos = sg.gpos;
+        es.gfirst = sg.gfirst;
+        const float* tau = args.tau + sg.tau_off;
+        if (sg.gfirst) st.open();
+        const int nchunk = kMode == M_EXACT ? (sg.npad + kExactNC - 1) / kExactNC : 1;
+        for (int cc = 0; cc < nchunk; ++cc, ++chunk_it) {
+          if (!mbar_wait(tmem_full, chunk_it & 1u, abort_flag, tb.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int c_lo = kMode == M_EXACT ? cc * kExactNC : 0;
+          const int c_hi = kMode == M_EXACT ? min(sg.n, c_lo + kExactNC) : sg.n;
+          for (int c = c_lo; c < c_hi; c += 32) {
+            float v[32];
+            if constexpr (kMode == M_EXACT) {
+              float g1[32], g2[32], g3[32];
+              const uint32_t lc = (uint32_t)(c - c_lo);
+              tmem_ld32(t_lane + lc, v);
+              tmem_ld32(t_lane + kExactNC + lc, g1);
+              tmem_ld32(t_lane + 2 * kExactNC + lc, g2);
+              tmem_ld32(t_lane + 3 * kExactNC + lc, g3);
+              const float base = sig * 6.103515625e-05f;  // sigma 2^-14
+#pragma unroll
+              for (int k = 0; k < 32; ++k) {
+                float t = fmaf(g3[k], 0.0078125f, g2[k]);
+                t = fmaf(t, 0.0078125f, g1[k]);
+                t = fmaf(t, 0.0078125f, v[k]);
+                v[k] = (c + k < c_hi) ? t * (base * tau[c + k]) : 0.f;
+              }
+            } else {
+              tmem_ld32(t_lane + (uint32_t)c, v);
+            }
+            epi_chunk(kind, v, c, min(32, c_hi - c), es, st);
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tmem_empty);
+        }
+        if (ok && sg.glast) gsum += st.close(kind, sg.gn);
+      }
+      if (!ok) break;
       rowG[ci * kTileM + r] = gsum;
     }
   } else if (warp == 8) {
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
-      uint32_t it = 0, seg_it = 0;
-      for (int ci = 0; ci < F.ncomp && !*abort_flag; ++ci) {
-        const Component C = tb.comp[F.comp0 + ci];
-        for (int si = 0; si < C.nseg && !*abort_flag; ++si, ++seg_it) {
-          const Segment sg = tb.seg[C.seg0 + si];
-          const int nslab = (sg.npad + kKs - 1) / kKs;
-          const int n0 = sg.npad > 256 ? 256 : sg.npad;  // N split: <= 256 per MMA
-          const int n1 = sg.npad - n0;
-          const uint32_t id0 = idesc_make(kFmt, kTileM, (uint32_t)n0);
-          const uint32_t id1 = idesc_make(kFmt, kTileM, (uint32_t)(n1 > 0 ? n1 : 16));
-          if (!mbar_wait(tmem_empty, (seg_it & 1u) ^ 1u, abort_flag, tb.status)) break;
-          tc_fence_after();
-          bool ok = true;
-          for (int t = 0; t < nslab; ++t, ++it) {
-            const int stage = it % args.nstage;
-            const uint32_t ph = (it / args.nstage) & 1u;
-            if (!mbar_wait(&full[stage], ph, abort_flag, tb.status)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t a_hi = smem_u32(stages + (size_t)stage * args.stage_bytes);
-            const uint32_t a_lo = a_hi + kATileBytes;
-            const uint32_t b_hi = a_hi + 2 * kATileBytes;
-            const uint32_t b_lo = b_hi + (uint32_t)(sg.npad * kRowBytes);
-#pragma unroll
-            for (int kk = 0; kk < kKsteps; ++kk) {
-              const uint32_t ko = (uint32_t)(kk * kMmaK * kEl);  // 32 B per K step
-              const uint64_t dah = sdesc_sw64(a_hi + ko), dal = sdesc_sw64(a_lo + ko);
-              for (int h = 0; h < (n1 > 0 ? 2 : 1); ++h) {
-                const uint32_t boff = (uint32_t)(h * n0 * kRowBytes) + ko;
-                const uint64_t dbh = sdesc_sw64(b_hi + boff), dbl = sdesc_sw64(b_lo + boff);
-                const uint32_t dt = tmem_base + (uint32_t)(h * n0);
-                const uint32_t idd = h ? id1 : id0;
-                const uint32_t accum = (t > 0 || kk > 0) ? 1u : 0u;
-                tc_mma<kBf16>(dt, dah, dbh, idd, accum);
-                tc_mma<kBf16>(dt, dah, dbl, idd, 1u);
-                tc_mma<kBf16>(dt, dal, dbh, idd, 1u);
-              }
+      uint32_t it = 0, chunk_it = 0;
+      bool ok = true;
+      for (int ci = 0; ci < F.ncomp && ok && !*abort_flag; ++ci) {
+        const Component Cm = tb.comp[F.comp0 + ci];
+        for (int si = 0; si < Cm.nseg && ok; ++si) {
+          const Segment sg = tb.seg[Cm.seg0 + si];
+          const int nslab = sg.npad / kKs;
+          const int nchunk = kMode == M_EXACT ? (sg.npad + kExactNC - 1) / kExactNC : 1;
+          for (int cc = 0; cc < nchunk && ok; ++cc, ++chunk_it) {
+            const int nc = kMode == M_EXACT ? min(kExactNC, sg.npad - cc * kExactNC) : sg.npad;
+            const int n0 = nc > 256 ? 256 : nc;  // N per MMA <= 256
+            const int n1 = nc - n0;
+            const uint32_t id0 = idesc_make(C::kFmt, kTileM, (uint32_t)n0);
+            const uint32_t id1 = idesc_make(C::kFmt, kTileM, (uint32_t)(n1 > 0 ? n1 : 16));
+            if (!mbar_wait(tmem_empty, (chunk_it & 1u) ^ 1u, abort_flag, tb.status)) {
+              ok = false;
+              break;
             }
-            tc_commit(&empty[stage]);  // frees the stage when these MMAs retire
+            tc_fence_after();
+            for (int t = 0; t < nslab; ++t, ++it) {
+              const int stage = it % args.nstage;
+              const uint32_t ph = (it / args.nstage) & 1u;
+              if (!mbar_wait(&full[stage], ph, abort_flag, tb.status)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t sa = smem_u32(stages + (size_t)stage * args.stage_bytes);
+              const uint32_t sb = sa + kParts * kPartBytes;
+              const uint32_t bpart = (uint32_t)(nc * kRowBytes);
+#pragma unroll
+              for (int kk = 0; kk < kKsteps; ++kk) {
+                const uint32_t ko = (uint32_t)(kk * C::kMmaK * kEl);  // 32 B per K step
+                const uint32_t first = (t == 0 && kk == 0) ? 0u : 1u;
+                if constexpr (kMode == M_EXACT) {
+                  // slice pairs (a, b) of weight a + b = w <= 3 into accumulator w
+#pragma unroll
+                  for (int w = 0; w < 4; ++w) {
+                    const uint32_t dt = tmem_base + (uint32_t)(w * kExactNC);
+#pragma unroll
+                    for (int a = 0; a <= w; ++a) {
+                      const uint64_t da = sdesc_sw64(sa + a * kPartBytes + ko);
+                      const uint64_t db = sdesc_sw64(sb + (w - a) * bpart + ko);
+                      tc_mma<false>(dt, da, db, id0, (a == 0) ? first : 1u);
+                    }
+                  }
+                } else {
+                  const uint64_t dah = sdesc_sw64(sa + ko), dal = sdesc_sw64(sa + kPartBytes + ko);
+                  for (int h = 0; h < (n1 > 0 ? 2 : 1); ++h) {
+                    const uint32_t boff = (uint32_t)(h * n0 * kRowBytes) + ko;
+                    const uint64_t dbh = sdesc_sw64(sb + boff), dbl = sdesc_sw64(sb + bpart + boff);
+                    const uint32_t dt = tmem_base + (uint32_t)(h * n0);
+                    const uint32_t idd = h ? id1 : id0;
+                    tc_mma<kMode == M_TF32>(dt, dah, dbh, idd, first);
+                    tc_mma<kMode == M_TF32>(dt, dah, dbl, idd, 1u);
+                    tc_mma<kMode == M_TF32>(dt, dal, dbh, idd, 1u);
+                  }
+                }
+              }
+              tc_commit(&empty[stage]);  // frees the stage when these MMAs retire
+            }
+            if (ok) tc_commit(tmem_full);  // this chunk's accumulators complete
           }
-          if (!ok) break;
-          tc_commit(tmem_full);  // accumulator of this block complete
         }
       }
     }
@@ -437,22 +747,30 @@ __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
     // ------------------------------------------------------------- B loads
     if (lane == 0) {
       uint32_t it = 0;
-      for (int ci = 0; ci < F.ncomp && !*abort_flag; ++ci) {
-        const Component C = tb.comp[F.comp0 + ci];
-        for (int si = 0; si < C.nseg && !*abort_flag; ++si) {
-          const Segment sg = tb.seg[C.seg0 + si];
-          const int nslab = (sg.npad + kKs - 1) / kKs;
-          const uint32_t bytes = (uint32_t)(2 * sg.npad * kRowBytes);
-          // img_off counts floats; a block's BF16 image follows its TF32 one
-          const long long tf32_floats = (long long)((sg.npad + 15) / 16) * 2 * sg.npad * kRowBytes / 4;
-          const uint8_t* src = args.img + ((size_t)sg.img_off + (kBf16 ? tf32_floats : 0)) * 4;
-          for (int t = 0; t < nslab; ++t, ++it) {
-            const int stage = it % args.nstage;
-            const uint32_t ph = (it / args.nstage) & 1u;
-            if (!mbar_wait(&empty[stage], ph ^ 1u, abort_flag, tb.status)) break;
-            uint8_t* dst = stages + (size_t)stage * args.stage_bytes + 2 * kATileBytes;
-            mbar_arrive_expect_tx(&full[stage], bytes);
-            bulk_g2s(dst, src + (size_t)t * bytes, bytes, &full[stage]);
+      bool ok = true;
+      for (int ci = 0; ci < F.ncomp && ok && !*abort_flag; ++ci) {
+        const Component Cm = tb.comp[F.comp0 + ci];
+        for (int si = 0; si < Cm.nseg && ok; ++si) {
+          const Segment sg = tb.seg[Cm.seg0 + si];
+          const int nslab = sg.npad / kKs;
+          const int nchunk = kMode == M_EXACT ? (sg.npad + kExactNC - 1) / kExactNC : 1;
+          const long long fl = image_floats(sg.npad);
+          const uint8_t* base = args.img + ((size_t)sg.img_off + (size_t)kMode * fl) * 4;
+          for (int cc = 0; cc < nchunk && ok; ++cc) {
+            const int nc = kMode == M_EXACT ? min(kExactNC, sg.npad - cc * kExactNC) : sg.npad;
+            const uint32_t bytes = (uint32_t)(kParts * nc * kRowBytes);
+            const uint8_t* src = base + (size_t)cc * nslab * kParts * kExactNC * kRowBytes;
+            for (int t = 0; t < nslab; ++t, ++it) {
+              const int stage = it % args.nstage;
+              const uint32_t ph = (it / args.nstage) & 1u;
+              if (!mbar_wait(&empty[stage], ph ^ 1u, abort_flag, tb.status)) {
+                ok = false;
+                break;
+              }
+              uint8_t* dst = stages + (size_t)stage * args.stage_bytes + kParts * kPartBytes;
+              mbar_arrive_expect_tx(&full[stage], bytes);
+              bulk_g2s(dst, src + (size_t)t * bytes, bytes, &full[stage]);
+            }
           }
         }
       }
@@ -490,69 +808,134 @@ __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
 }
 
 // ----------------------------------------------------- operand image builder
-// For one block (rotated or identity) writes, per K-stage t, the hi image
-// (npad rows x 64 B, swizzled) followed by the lo image.  R entries beyond n
-// are zero.  Split from FP64: hi = round(R), lo = round(R - hi).
+// For one block (rotated or identity) writes its three images:
+//   TF32/BF16: per K stage t, the hi part (npad rows x 64 B, swizzled) then
+//              the lo part; hi = round(R), lo = round(R - hi) from FP64.
+//   EXACT:     per N chunk of 128 rows, per K stage of 32 columns, the four
+//              integer slices of R_i / tau_i (tau_i = 2^f > max_j |R_ij|),
+//              nc rows x 64 B each; tau_i goes to the tau pool.
+// Entries beyond n are zero.
 struct ImgJob {
   long long r_off;     // FP64 block (or -1 for identity)
   long long img_off;   // destination, in floats (4-byte units)
+  long long tau_off;
   int n, npad;
 };
 
-template <bool kBf16>
-__global__ void build_image_kernel(const ImgJob* jobs, const double* R, uint8_t* img) {
-  constexpr int kKs = kBf16 ? 32 : 16;
-  constexpr int kEl = kBf16 ? 2 : 4;
+__device__ inline double r_entry(const ImgJob& J, const double* R, int row, int col) {
+  if (row >= J.n || col >= J.n) return 0.0;
+  return (J.r_off >= 0) ? R[J.r_off + (long long)row * J.n + col] : (row == col ? 1.0 : 0.0);
+}
+
+__global__ void build_image_kernel(const ImgJob* jobs, const double* R, uint8_t* img,
+                                   float* tau) {
   const ImgJob J = jobs[blockIdx.x];
-  const int nslab = (J.npad + kKs - 1) / kKs;
-  const long long total = (long long)nslab * J.npad * kKs;
+  const long long fl = image_floats(J.npad);
   uint8_t* base = img + (size_t)J.img_off * 4;
-  const uint32_t slab_bytes = (uint32_t)(2 * J.npad * kRowBytes);
+  const int npad = J.npad;
+  for (int row = threadIdx.x; row < npad; row += blockDim.x) {
+    double mx = 0.0;
+    for (int c = 0; c < J.n; ++c) mx = fmax(mx, fabs(r_entry(J, R, row, c)));
+    int e = 0;
+    if (mx > 0.0) e = ilogb(mx * 1.0009765625) + 1;
+    tau[J.tau_off + row] = ldexpf(1.f, e);
+  }
+  __syncthreads();
+  const int nslab32 = npad / 32;
+  const long long total = (long long)npad * npad;
   for (long long e = threadIdx.x; e < total; e += blockDim.x) {
-    const int t = (int)(e / ((long long)J.npad * kKs));
-    const int rem = (int)(e - (long long)t * J.npad * kKs);
-    const int row = rem / kKs, k = rem - row * kKs;
-    const int col = t * kKs + k;
-    double v = 0.0;
-    if (row < J.n && col < J.n) v = (J.r_off >= 0) ? R[J.r_off + (long long)row * J.n + col]
-                                                   : (row == col ? 1.0 : 0.0);
-    uint8_t* hi = base + (size_t)t * slab_bytes;
-    uint8_t* lo = hi + J.npad * kRowBytes;
-    const uint32_t off = swz64((uint32_t)row, (uint32_t)(k * kEl));
-    if constexpr (kBf16) {
-      __nv_bfloat16 h = __double2bfloat16(v);
-      __nv_bfloat16 l = __double2bfloat16(v - (double)__bfloat162float(h));
-      *reinterpret_cast<__nv_bfloat16*>(hi + off) = h;
-      *reinterpret_cast<__nv_bfloat16*>(lo + off) = l;
-    } else {
-      uint32_t h = to_tf32((float)v);
-      uint32_t l = to_tf32((float)(v - (double)__uint_as_float(h)));
+    const int row = (int)(e / npad), col = (int)(e - (long long)row * npad);
+    const double v = r_entry(J, R, row, col);
+    {  // TF32: stage t = col / 16
+      const int t = col / 16, k = col % 16;
+      uint8_t* hi = base + (size_t)t * (2 * npad * kRowBytes);
+      uint8_t* lo = hi + npad * kRowBytes;
+      const uint32_t off = swz64((uint32_t)row, (uint32_t)(k * 4));
+      const uint32_t h = to_tf32((float)v);
+      const uint32_t l = to_tf32((float)(v - (double)__uint_as_float(h)));
       *reinterpret_cast<uint32_t*>(hi + off) = h;
       *reinterpret_cast<uint32_t*>(lo + off) = l;
+    }
+    {  // BF16: stage t = col / 32
+      const int t = col / 32, k = col % 32;
+      uint8_t* hi = base + (size_t)fl * 4 + (size_t)t * (2 * npad * kRowBytes);
+      uint8_t* lo = hi + npad * kRowBytes;
+      const uint32_t off = swz64((uint32_t)row, (uint32_t)(k * 2));
+      const __nv_bfloat16 h = __double2bfloat16(v);
+      const __nv_bfloat16 l = __double2bfloat16(v - (double)__bfloat162float(h));
+      *reinterpret_cast<__nv_bfloat16*>(hi + off) = h;
+      *reinterpret_cast<__nv_bfloat16*>(lo + off) = l;
+    }
+    {  // EXACT: chunk cc = row / 128, stage t = col / 32
+      const int cc = row / kExactNC, rr = row % kExactNC;
+      const int nc = min(kExactNC, npad - cc * kExactNC);
+      const int t = col / 32, k = col % 32;
+      uint8_t* st = base + (size_t)2 * fl * 4 +
+                    ((size_t)cc * nslab32 * 4 * kExactNC + (size_t)t * 4 * nc) * kRowBytes;
+      const uint32_t off = swz64((uint32_t)rr, (uint32_t)(k * 2));
+      double w = v / (double)tau[J.tau_off + row] * 128.0;  // exact: tau is 2^f
+      for (int s = 0; s < 4; ++s) {
+        const double yv = rint(w);
+        *reinterpret_cast<__nv_bfloat16*>(st + (size_t)s * nc * kRowBytes + off) =
+            __double2bfloat16(yv);
+        w = (w - yv) * 128.0;
+      }
     }
   }
 }
 
-__global__ void split_o_kernel(const double* operm, float* ohi, float* olo, long long n) {
+__global__ void split_o_kernel(const double* operm, const double* o_nat, float* ohi, float* olo,
+                               float* onat, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const double o = operm[i];
     const float h = (float)o;
     ohi[i] = h;
     olo[i] = (float)(o - (double)h);
+    onat[i] = (float)o_nat[i];
   }
 }
 
 int npad_of(int n) { return (n + 31) / 32 * 32; }
 
-// bytes of one block's image (both precisions use the same byte count per
-// element pair: TF32 slabs of 16 x 4 B, BF16 slabs of 32 x 2 B)
-long long image_floats(int npad) {
-  const long long slabs16 = (npad + 15) / 16;
-  return slabs16 * 2LL * npad * kRowBytes / 4;
+template <int kMode>
+size_t stage_bytes_for(int ncmax) {
+  return (size_t)MC<kMode>::kParts * kPartBytes + (size_t)MC<kMode>::kParts * ncmax * kRowBytes;
+}
+size_t ctrl_bytes() {  // barriers (<= 256 B) + per-row tables + block table
+  return 256 + 2 * sizeof(double) * kMaxComponents * kTileM + sizeof(float) * kSigRing * kTileM +
+         3 * sizeof(float) * kMaxNpad;
 }
 
-size_t stage_bytes_for(int npad_max) { return 2 * kATileBytes + 2 * (size_t)npad_max * kRowBytes; }
+template <int kMode>
+cudaError_t launch_mode(const MmaPlan& p, const Tables& tb, const Function& F, const float* x,
+                        int N, float* out, cudaStream_t st) {
+  const int npad_max = npad_of(F.max_n);
+  const int ncmax = kMode == M_EXACT ? std::min(npad_max, kExactNC) : npad_max;
+  const size_t sb = stage_bytes_for<kMode>(ncmax);
+  const size_t ctrl = ctrl_bytes();
+  const int nstage = (int)std::min<size_t>(4, (219 * 1024 - ctrl) / sb);
+  if (nstage < 2) return cudaErrorInvalidValue;
+  const size_t smem = nstage * sb + ctrl + 1024;  // + alignment slack
+  MmaArgs a;
+  a.tb = tb;
+  a.F = F;
+  a.x = x;
+  a.out = out;
+  a.N = N;
+  a.ohi = p.ohi;
+  a.olo = p.olo;
+  a.img = reinterpret_cast<const uint8_t*>(p.img);
+  a.tau = p.tau;
+  a.onat = p.onat;
+  a.nstage = nstage;
+  a.stage_bytes = (int)sb;
+  cudaError_t e = cudaFuncSetAttribute(mma_eval_kernel<kMode>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  mma_eval_kernel<kMode><<<(unsigned)((N + kTileM - 1) / kTileM), kThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -560,33 +943,39 @@ size_t stage_bytes_for(int npad_max) { return 2 * kATileBytes + 2 * (size_t)npad
 curob_status mma_prepare(MmaPlan& p, std::vector<Segment>& segs, const Tables& tb, float* prev) {
   (void)prev;
   mma_release(p);
-  int dev = 0, cc_major = 0, cc_minor = 0;
+  int dev = 0, cc_major = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&cc_major, cudaDevAttrComputeCapabilityMajor, dev);
-  cudaDeviceGetAttribute(&cc_minor, cudaDevAttrComputeCapabilityMinor, dev);
   p.ready = false;
-  // layout: per segment, a TF32 image then a BF16 image of the same size
-  long long off = 0;
+  // per block: [TF32 | BF16 | EXACT] images and npad tau entries
+  long long off = 0, toff = 0;
   for (Segment& s : segs) {
     s.npad = npad_of(s.n);
     if (s.npad > kMaxNpad) {
       s.img_off = -1;
+      s.tau_off = 0;
       continue;
     }
     s.img_off = off;
-    off += 2 * image_floats(s.npad);
+    off += 3 * image_floats(s.npad);
+    s.tau_off = toff;
+    toff += s.npad;
   }
   p.img_floats = off;
   if (off > 0 && cudaMalloc(&p.img, sizeof(float) * (size_t)off) != cudaSuccess) {
     cudaGetLastError();
     return CUROB_ERR_OUT_OF_MEMORY;
   }
-  // o[S] split, one entry per (component, variable)
+  if (cudaMalloc(&p.tau, sizeof(float) * (size_t)std::max<long long>(toff, 1)) != cudaSuccess) {
+    cudaGetLastError();
+    return CUROB_ERR_OUT_OF_MEMORY;
+  }
   int max_comp = 0;
   for (const Segment& s : segs) max_comp = std::max(max_comp, s.comp + 1);
   p.o_entries = (long long)max_comp * tb.D;
-  if (cudaMalloc(&p.ohi, sizeof(float) * (size_t)std::max<long long>(p.o_entries, 1)) != cudaSuccess ||
-      cudaMalloc(&p.olo, sizeof(float) * (size_t)std::max<long long>(p.o_entries, 1)) != cudaSuccess) {
+  const size_t ob = sizeof(float) * (size_t)std::max<long long>(p.o_entries, 1);
+  if (cudaMalloc(&p.ohi, ob) != cudaSuccess || cudaMalloc(&p.olo, ob) != cudaSuccess ||
+      cudaMalloc(&p.onat, ob) != cudaSuccess) {
     cudaGetLastError();
     return CUROB_ERR_OUT_OF_MEMORY;
   }
@@ -601,7 +990,7 @@ curob_status mma_prepare(MmaPlan& p, std::vector<Segment>& segs, const Tables& t
 
 curob_status mma_refresh(MmaPlan& p, const std::vector<Segment>& segs, const std::vector<int>& ids,
                          const Tables& tb) {
-  std::vector<ImgJob> jobs16, jobs32;
+  std::vector<ImgJob> jobs;
   for (int id : ids) {
     const Segment& s = segs[id];
     if (s.img_off < 0) continue;
@@ -610,20 +999,16 @@ curob_status mma_refresh(MmaPlan& p, const std::vector<Segment>& segs, const std
     J.n = s.n;
     J.npad = s.npad;
     J.img_off = s.img_off;
-    jobs32.push_back(J);
-    J.img_off = s.img_off + image_floats(s.npad);
-    jobs16.push_back(J);
+    J.tau_off = s.tau_off;
+    jobs.push_back(J);
   }
-  if (!jobs32.empty()) {
+  if (!jobs.empty()) {
     ImgJob* d = nullptr;
-    const size_t bytes = sizeof(ImgJob) * jobs32.size();
-    if (cudaMalloc(&d, 2 * bytes) != cudaSuccess) return CUROB_ERR_OUT_OF_MEMORY;
-    cudaError_t e = cudaMemcpy(d, jobs32.data(), bytes, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(d + jobs32.size(), jobs16.data(), bytes, cudaMemcpyHostToDevice);
+    const size_t bytes = sizeof(ImgJob) * jobs.size();
+    if (cudaMalloc(&d, bytes) != cudaSuccess) return CUROB_ERR_OUT_OF_MEMORY;
+    cudaError_t e = cudaMemcpy(d, jobs.data(), bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-      build_image_kernel<false><<<(unsigned)jobs32.size(), 256>>>(d, tb.R, (uint8_t*)p.img);
-      build_image_kernel<true><<<(unsigned)jobs16.size(), 256>>>(d + jobs32.size(), tb.R,
-                                                                 (uint8_t*)p.img);
+      build_image_kernel<<<(unsigned)jobs.size(), 256>>>(d, tb.R, (uint8_t*)p.img, p.tau);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -631,7 +1016,7 @@ curob_status mma_refresh(MmaPlan& p, const std::vector<Segment>& segs, const std
     if (e != cudaSuccess) return CUROB_ERR_CUDA;
   }
   if (p.o_entries > 0) {
-    split_o_kernel<<<256, 256>>>(tb.operm, p.ohi, p.olo, p.o_entries);
+    split_o_kernel<<<256, 256>>>(tb.operm, tb.o, p.ohi, p.olo, p.onat, p.o_entries);
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
       return CUROB_ERR_CUDA;
   }
@@ -642,8 +1027,10 @@ void mma_release(MmaPlan& p) {
   cudaFree(p.img);
   cudaFree(p.ohi);
   cudaFree(p.olo);
+  cudaFree(p.tau);
+  cudaFree(p.onat);
   p.img = nullptr;
-  p.ohi = p.olo = nullptr;
+  p.ohi = p.olo = p.tau = p.onat = nullptr;
   p.img_floats = 0;
   p.o_entries = 0;
   p.ready = false;
@@ -655,46 +1042,18 @@ bool mma_supports(const MmaPlan& p, const Function& F) {
 
 int mma_auto_mode(const MmaPlan& p, const Function& F) {
   (void)p;
-  // FP32 accumulation in TMEM truncates: |z| shrinks by ~2e-6 relative over
-  // a 334-long block, too much for the kinds that magnify z errors.
-  return F.sensitive ? CUROB_PRECISION_SIMT : CUROB_PRECISION_TF32X3;
+  return F.sensitive ? CUROB_PRECISION_EXACT : CUROB_PRECISION_TF32X3;
 }
 
-cudaError_t launch_mma(const MmaPlan& p, const Tables& tb, const Function& F, bool bf16,
+cudaError_t launch_mma(const MmaPlan& p, const Tables& tb, const Function& F, int mode,
                        const float* x, int N, float* out, cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
-  const int npad_max = npad_of(F.max_n);
-  const size_t sb = stage_bytes_for(npad_max);
-  const size_t ctrl = 256 + 2 * sizeof(double) * kMaxComponents * kTileM;
-  int nstage = (int)std::min<size_t>(4, (219 * 1024 - ctrl) / sb);
-  if (nstage < 2) return cudaErrorInvalidValue;
-  const size_t smem = nstage * sb + ctrl + 1024;  // + alignment slack
-  MmaArgs a;
-  a.tb = tb;
-  a.F = F;
-  a.x = x;
-  a.out = out;
-  a.N = N;
-  a.ohi = p.ohi;
-  a.olo = p.olo;
-  a.img = reinterpret_cast<const uint8_t*>(p.img);
-  a.nstage = nstage;
-  a.stage_bytes = (int)sb;
-  a.b_bytes_max = 2 * npad_max * kRowBytes;
-  // the BF16 image of a block sits image_floats(npad) floats after its TF32 one
-  cudaError_t e;
-  if (bf16) {
-    e = cudaFuncSetAttribute(mma_eval_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    mma_eval_kernel<true><<<(unsigned)((N + kTileM - 1) / kTileM), kThreads, smem, st>>>(a);
-  } else {
-    e = cudaFuncSetAttribute(mma_eval_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    mma_eval_kernel<false><<<(unsigned)((N + kTileM - 1) / kTileM), kThreads, smem, st>>>(a);
+  switch (mode) {
+    case CUROB_PRECISION_TF32X3: return launch_mode<M_TF32>(p, tb, F, x, N, out, st);
+    case CUROB_PRECISION_BF16X3: return launch_mode<M_BF16>(p, tb, F, x, N, out, st);
+    case CUROB_PRECISION_EXACT: return launch_mode<M_EXACT>(p, tb, F, x, N, out, st);
+    default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 }  // namespace curob

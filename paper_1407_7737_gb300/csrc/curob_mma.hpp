@@ -14,6 +14,8 @@ struct MmaPlan {
   float* ohi = nullptr;      // o[S[k]] split into FP32 hi/lo words, per component
   float* olo = nullptr;
   long long o_entries = 0;
+  float* tau = nullptr;      // EXACT: power-of-two row scales of every block
+  float* onat = nullptr;     // o per component in natural order, FP32
   bool sm103 = false;        // the device runs tcgen05
   bool ready = false;
 };
@@ -26,9 +28,10 @@ curob_status mma_refresh(MmaPlan& p, const std::vector<Segment>& segs, const std
 void mma_release(MmaPlan& p);
 // True when every block of F fits the tensor-core kernel.
 bool mma_supports(const MmaPlan& p, const Function& F);
-// Precision AUTO picks for F (CUROB_PRECISION_TF32X3 or _BF16X3).
+// Precision AUTO picks for F (CUROB_PRECISION_TF32X3 or _EXACT).
 int mma_auto_mode(const MmaPlan& p, const Function& F);
-cudaError_t launch_mma(const MmaPlan& p, const Tables& tb, const Function& F, bool bf16,
+// mode: CUROB_PRECISION_TF32X3, _BF16X3 or _EXACT.
+cudaError_t launch_mma(const MmaPlan& p, const Tables& tb, const Function& F, int mode,
                        const float* x, int N, float* out, cudaStream_t st);
 
 }  // namespace curob

@@ -51,7 +51,7 @@ def test_calls_before_initialize_fail_cleanly(lib):
     assert cu.curob_evaluatef(0, 0, 1, 0, None, check=False) == NI
     assert cu.curob_dispose(check=False) == NI
     assert cu.curob_get_device_status(None, check=False) == NI
-    assert cu.curob_set_precision(7, check=False) == cu.CODES["CUROB_ERR_INVALID_ARGUMENT"]
+    assert cu.curob_set_precision(9, check=False) == cu.CODES["CUROB_ERR_INVALID_ARGUMENT"]
 
 
 def test_product_path_does_not_import_the_oracle():
