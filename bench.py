@@ -264,6 +264,10 @@ def run_curob(args):
             fp64_ms += a.elapsed_time(b)
         fp64 = NFUN * N / (fp64_ms / 1e3)
 
+    ragged = None
+    if rank == 0 and not args.no_extra:
+        ragged = ragged_batch(cu, torch, dev, stream, reps=max(3, args.steps))
+
     # roofline of the dominant kernel (the path holding most of the step)
     pk, src = peaks()
     flops = np.array([algorithmic_flops(cu, f) * N for f in range(NFUN)], dtype=np.float64)
@@ -328,13 +332,61 @@ def run_curob(args):
             "per_function_ms": [round(v, 4) for v in launch_ms.tolist()],
             "per_function_path": [{1: "tf32x3", 2: "bf16x3", 3: "simt", 4: "exact"}[m]
                                   for m in modes],
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "ragged_batch": ragged,
             "clocks": clk.summary(), "gpu_launches": gpu_launches,
         }
         print(json.dumps(line))
     cu.curob_dispose()
     if pg is not None:
         pg.destroy_process_group()
+
+
+def ragged_batch(cu, torch, dev, stream, reps=5, n_items=64, seed=2024):
+    """64 items, fid uniform over the suite, D uniform over {10, 30, 50, 100,
+    500, 1000}, N log-uniform in [32, 8192]: one persistent launch replayed
+    from a CUDA graph against one launch per item (same EXACT arithmetic)."""
+    from paper_1407_7737_gb300 import inputs
+    items = inputs.ragged_instances(n_items, seed)
+    xs, outs, spec = [], [], []
+    for i, (fid, D, N) in enumerate(items):
+        x = torch.empty((N, D), dtype=torch.float32, device=dev).uniform_(-100.0, 100.0)
+        o = torch.empty(N, dtype=torch.float32, device=dev)
+        xs.append(x)
+        outs.append(o)
+        spec.append((fid, D, 1000 + D, N, x, o))
+    b = cu.curob_batch_create(spec)
+    evals = sum(N for (_, _, N) in items)
+    try:
+        cu.curob_batch_run(b, stream)  # autotune + capture
+        cu.curob_batch_status(b, stream)
+
+        def timed(fn):
+            fn(b, stream)
+            a = torch.cuda.Event(enable_timing=True)
+            z = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            for _ in range(reps):
+                fn(b, stream)
+            z.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(z) / reps
+
+        ms_p = timed(cu.curob_batch_run)
+        ms_s = timed(cu.curob_batch_run_separate)
+        cu.curob_batch_status(b, stream)
+        nwork, grid, order = cu.curob_batch_schedule(b)
+    finally:
+        cu.curob_batch_destroy(b)
+    return {"items": n_items, "evals_per_run": evals,
+            "dims": sorted({D for (_, D, _) in items}),
+            "persistent_graph_ms": round(ms_p, 4), "separate_launches_ms": round(ms_s, 4),
+            "persistent_evals_s": round(evals / (ms_p / 1e3), 1),
+            "separate_evals_s": round(evals / (ms_s / 1e3), 1),
+            "speedup": round(ms_s / ms_p, 3),
+            "schedule": {"work_items": nwork, "grid": grid,
+                         "order": ["longest-first", "round-robin", "item-order"][order]},
+            "precision": "exact (all items)"}
 
 
 def cpu_baseline(sample_n=8, budget_s=25.0):

@@ -148,6 +148,57 @@ curob_status curob_set_component(int fid, int comp, const double* o, const int* 
  * Sec. 6: the member with the smallest bias).  Host pointer, D doubles. */
 curob_status curob_get_optimum(int fid, double* xopt);
 
+/* ---------------------------------------------------------------------------
+ * Ragged batches (this library's extension; the paper evaluates one function
+ * at one D at a time).  A batch is a list of (function, D, seed, population)
+ * items evaluated together by one persistent tensor-core kernel: each CTA of
+ * a grid of at most one CTA per SM takes 128-candidate tiles of any item from
+ * a work counter until none is left.  Every item uses the EXACT contraction
+ * (curob_precision), so any function at any block width up to 512 meets the
+ * FP32 tolerance.  The first curob_batch_run times a few schedules (work
+ * order, grid size), keeps the fastest, and captures it in a CUDA graph that
+ * later runs replay.  A batch owns its instances (one per distinct D, seed);
+ * it is independent of curob_initialize.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int fid;          /* Table 1 ID */
+  int D;            /* dimension: >= 2, >= 10 for IDs 23..28, 35, 36, blocks <= 512 */
+  uint64_t seed;    /* instance seed (as curob_initialize) */
+  int N;            /* candidates, >= 0 */
+  const float* x;   /* device pointer, N x D row-major, read at every run */
+  float* out;       /* device pointer, N values, written at every run */
+} curob_batch_item;
+
+typedef struct curob_batch_st* curob_batch;
+
+/* Builds the instances and the work list of n_items items (host array).
+ * Pointers inside items must stay valid for the life of the batch.  Errors:
+ * NULL_POINTER, INVALID_ARGUMENT (n_items < 1, N < 0, host pointers),
+ * INVALID_FID, INVALID_DIM, UNSUPPORTED (a block wider than 512, or a device
+ * without tcgen05), OUT_OF_MEMORY, CUDA.  Synchronous. */
+curob_status curob_batch_create(const curob_batch_item* items, int n_items, curob_batch* batch);
+
+/* Evaluates every item on `stream` (asynchronous): the first call autotunes
+ * and captures the CUDA graph (it synchronises the stream while timing and
+ * must not be made during a stream capture); later calls launch the graph. */
+curob_status curob_batch_run(curob_batch batch, curob_stream_t stream);
+
+/* The same work as one launch of the tensor-core kernel per item, in item
+ * order (the baseline the persistent launch is measured against). */
+curob_status curob_batch_run_separate(curob_batch batch, curob_stream_t stream);
+
+/* Schedule chosen by the autotuner (host pointers, any may be NULL): number
+ * of work items, grid size, order (0 = longest first, 1 = round robin over
+ * items, 2 = item order).  NOT_INITIALIZED before the first run. */
+curob_status curob_batch_schedule(curob_batch batch, int* n_work, int* grid, int* order);
+
+/* Synchronises `stream` and reports (then clears) a device-side error of any
+ * of the batch's instances. */
+curob_status curob_batch_status(curob_batch batch, curob_stream_t stream);
+
+/* Releases the batch (synchronises the device first). */
+curob_status curob_batch_destroy(curob_batch batch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -44,6 +44,12 @@ _SIGS = [
     ("curob_get_component", _I, [_I, _I, _P, _P, _P]),
     ("curob_set_component", _I, [_I, _I, _P, _P, _P]),
     ("curob_get_optimum", _I, [_I, _P]),
+    ("curob_batch_create", _I, [_P, _I, _P]),
+    ("curob_batch_run", _I, [_P, _P]),
+    ("curob_batch_run_separate", _I, [_P, _P]),
+    ("curob_batch_schedule", _I, [_P, _P, _P, _P]),
+    ("curob_batch_status", _I, [_P, _P]),
+    ("curob_batch_destroy", _I, [_P]),
 ]
 EXPORTS = [s[0] for s in _SIGS]
 
@@ -205,6 +211,46 @@ def curob_get_optimum(fid):
     o = np.zeros(D)
     _call("curob_get_optimum", fid, o.ctypes.data)
     return o
+
+
+# ----- ragged batches ---------------------------------------------------------
+class BatchItem(ctypes.Structure):
+    _fields_ = [("fid", ctypes.c_int), ("D", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("N", ctypes.c_int), ("x", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+def curob_batch_create(items):
+    """items: sequence of (fid, D, seed, N, x, out) with x/out device tensors or
+    pointers.  Returns the opaque batch handle."""
+    arr = (BatchItem * len(items))()
+    for i, (fid, D, seed, N, x, out) in enumerate(items):
+        arr[i] = BatchItem(fid, D, seed, N, _ptr(x), _ptr(out))
+    h = ctypes.c_void_p()
+    _call("curob_batch_create", ctypes.addressof(arr), len(items), ctypes.addressof(h))
+    return h.value
+
+
+def curob_batch_run(batch, stream=None, check=True):
+    return _call("curob_batch_run", batch, _stream(stream), check=check)
+
+
+def curob_batch_run_separate(batch, stream=None, check=True):
+    return _call("curob_batch_run_separate", batch, _stream(stream), check=check)
+
+
+def curob_batch_schedule(batch):
+    n, g, o = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _call("curob_batch_schedule", batch, ctypes.addressof(n), ctypes.addressof(g),
+          ctypes.addressof(o))
+    return n.value, g.value, o.value
+
+
+def curob_batch_status(batch, stream=None, check=True):
+    return _call("curob_batch_status", batch, _stream(stream), check=check)
+
+
+def curob_batch_destroy(batch, check=True):
+    return _call("curob_batch_destroy", batch, check=check)
 
 
 # ----- tensor conveniences ---------------------------------------------------

@@ -22,8 +22,8 @@ EXTRA = {
     "curob_simt64.cu": ["-fmad=false"],
     "curob_setup.cu": ["-fmad=false"],
 }
-SOURCES = ["curob_api.cu", "curob_setup.cu", "curob_simt64.cu", "curob_simt32.cu",
-           "curob_mma.cu"]
+SOURCES = ["curob_api.cu", "curob_instance.cu", "curob_setup.cu", "curob_simt64.cu",
+           "curob_simt32.cu", "curob_mma.cu", "curob_batch.cu"]
 
 
 def _deps():

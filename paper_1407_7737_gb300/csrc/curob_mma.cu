@@ -45,6 +45,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "curob_mma.hpp"
 
@@ -350,64 +351,138 @@ __device__ __forceinline__ void epi_chunk(int kind, const float* v, int c, int c
 }
 
 // -------------------------------------------------------------- the kernel
-template <int kMode>
-__global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
-  using C = MC<kMode>;
-  constexpr int kKs = C::kKs, kEl = C::kEl, kParts = C::kParts;
-  constexpr int kKsteps = kKs / C::kMmaK;
+// Shared-memory map of a CTA (identical for the per-launch and the
+// persistent kernels).
+struct Smem {
+  uint8_t* stages;
+  uint64_t *full, *empty, *tmem_full, *tmem_empty, *sig_full, *prod_bar, *gbar;
+  uint32_t* tmem_slot;
+  volatile int* abort_flag;
+  double *rowG, *rowD2;
+  float* rowSig;
+  int* tabS;
+  float *tabH, *tabL;
+  int* item;  // persistent kernel: the work item of the CTA
+};
 
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
+__device__ inline Smem smem_map(uint8_t* smem_raw, int nstage, int stage_bytes) {
+  Smem m;
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  const Tables& tb = args.tb;
-  const Function& F = args.F;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  m.stages = smem;
+  uint8_t* ctrl = smem + (size_t)nstage * stage_bytes;
+  m.full = reinterpret_cast<uint64_t*>(ctrl);
+  m.empty = m.full + nstage;
+  m.tmem_full = m.empty + nstage;
+  m.tmem_empty = m.tmem_full + 1;
+  m.sig_full = m.tmem_empty + 1;  // [kSigRing]
+  m.prod_bar = m.sig_full + kSigRing;
+  m.gbar = m.prod_bar + 1;        // [nstage]
+  m.tmem_slot = reinterpret_cast<uint32_t*>(m.gbar + nstage);
+  m.abort_flag = reinterpret_cast<volatile int*>(m.tmem_slot + 1);
+  m.item = const_cast<int*>(reinterpret_cast<volatile int*>(m.abort_flag) + 1);
+  m.rowG = reinterpret_cast<double*>(ctrl + 256);                 // [kMaxComponents][128]
+  m.rowD2 = m.rowG + kMaxComponents * kTileM;                     // [kMaxComponents][128]
+  m.rowSig = reinterpret_cast<float*>(m.rowD2 + kMaxComponents * kTileM);  // [kSigRing][128]
+  m.tabS = reinterpret_cast<int*>(m.rowSig + kSigRing * kTileM);           // [kMaxNpad]
+  m.tabH = reinterpret_cast<float*>(m.tabS + kMaxNpad);
+  m.tabL = m.tabH + kMaxNpad;
+  return m;
+}
 
-  // layout: [stages][ctrl]
-  uint8_t* stages = smem;
-  uint8_t* ctrl = smem + (size_t)args.nstage * args.stage_bytes;
-  uint64_t* full = reinterpret_cast<uint64_t*>(ctrl);
-  uint64_t* empty = full + args.nstage;
-  uint64_t* tmem_full = empty + args.nstage;
-  uint64_t* tmem_empty = tmem_full + 1;
-  uint64_t* sig_full = tmem_empty + 1;                       // [kSigRing]
-  uint64_t* prod_bar = sig_full + kSigRing;
-  uint64_t* gbar = prod_bar + 1;                             // [nstage] gathers landed
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbar + args.nstage);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  double* rowG = reinterpret_cast<double*>(ctrl + 256);       // [kMaxComponents][128]
-  double* rowD2 = rowG + kMaxComponents * kTileM;             // [kMaxComponents][128]
-  float* rowSig = reinterpret_cast<float*>(rowD2 + kMaxComponents * kTileM);  // [kSigRing][128]
-  int* tabS = reinterpret_cast<int*>(rowSig + kSigRing * kTileM);             // [kMaxNpad]
-  float* tabH = reinterpret_cast<float*>(tabS + kMaxNpad);
-  float* tabL = tabH + kMaxNpad;
+// Barrier-phase counters of one role, carried from tile to tile.
+struct RoleState {
+  uint32_t it = 0;        // K stages
+  uint32_t chunk_it = 0;  // accumulator hand-offs
+  uint32_t pphase = 0;    // producer group barrier uses
+  uint32_t comp_it = 0;   // components (row-scale ring)
+};
 
+__device__ inline void cta_setup(const Smem& m, int nstage) {
+  const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < args.nstage; ++s) {
-      mbar_init(&full[s], 5);   // 4 producer warps + the B loader's expect_tx
-      mbar_init(&empty[s], 1);  // one tcgen05.commit
+    for (int s = 0; s < nstage; ++s) {
+      mbar_init(&m.full[s], 5);   // 4 producer warps + the B loader's expect_tx
+      mbar_init(&m.empty[s], 1);  // one tcgen05.commit
+      mbar_init(&m.gbar[s], 128); // producer threads' cp.async
     }
-    mbar_init(tmem_full, 1);
-    mbar_init(tmem_empty, 4);   // the 4 epilogue warps
-    for (int s = 0; s < kSigRing; ++s) mbar_init(&sig_full[s], 4);
-    mbar_init(prod_bar, 4);     // the 4 producer warps
-    for (int s = 0; s < args.nstage; ++s) mbar_init(&gbar[s], 128);  // producer threads' cp.async
-    *abort_flag = 0;
+    mbar_init(m.tmem_full, 1);
+    mbar_init(m.tmem_empty, 4);   // the 4 epilogue warps
+    for (int s = 0; s < kSigRing; ++s) mbar_init(&m.sig_full[s], 4);
+    mbar_init(m.prod_bar, 4);     // the 4 producer warps
+    *m.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 8) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
+                     smem_u32(m.tmem_slot)),
                  "r"(kMaxNpad));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem_base = *tmem_slot;
-  const long long row0 = (long long)blockIdx.x * kTileM;
-  const int D = tb.D;
+}
 
-  if (warp < 4) {
+// Epilogue threads write f of their rows once every role is done with the
+// tile (after a CTA barrier).
+__device__ inline void write_outputs(const MmaArgs& a, const Smem& m, long long row0) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < 4 || warp >= 8 || *m.abort_flag) return;
+  const int r = (warp - 4) * 32 + lane;
+  const long long grow = row0 + r;
+  if (grow >= a.N) return;
+  const Function& F = a.F;
+  double f;
+  if (F.composition) {
+    double G[kMaxComponents], d2v[kMaxComponents];
+    for (int ci = 0; ci < F.ncomp; ++ci) {
+      G[ci] = m.rowG[ci * kTileM + r];
+      d2v[ci] = m.rowD2[ci * kTileM + r];
+    }
+    f = compose(a.tb.comp + F.comp0, F.ncomp, G, d2v, a.tb.D);
+  } else {
+    f = m.rowG[r];
+  }
+  a.out[grow] = (float)(f + kFopt);
+}
+
+__device__ inline void cta_teardown(const Smem& m) {
+  const int warp = threadIdx.x >> 5;
+  if (warp == 8) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*m.tmem_slot),
+                 "r"(kMaxNpad));
+  }
+}
+
+#define CUROB_ROLE_PROLOGUE                                                   \
+  using C = MC<kMode>;                                                        \
+  constexpr int kKs = C::kKs, kEl = C::kEl, kParts = C::kParts;               \
+  constexpr int kKsteps = kKs / C::kMmaK;                                     \
+  (void)kEl; (void)kParts; (void)kKsteps;                                     \
+  const Tables& tb = a.tb;                                                    \
+  const Function& F = a.F;                                                    \
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;                 \
+  (void)lane;                                                                 \
+  uint8_t* stages = m.stages;                                                 \
+  uint64_t *full = m.full, *empty = m.empty, *tmem_full = m.tmem_full;        \
+  uint64_t *tmem_empty = m.tmem_empty, *sig_full = m.sig_full;                \
+  uint64_t *prod_bar = m.prod_bar, *gbar = m.gbar;                            \
+  volatile int* abort_flag = m.abort_flag;                                    \
+  double *rowG = m.rowG, *rowD2 = m.rowD2;                                    \
+  float* rowSig = m.rowSig;                                                   \
+  int* tabS = m.tabS;                                                         \
+  float *tabH = m.tabH, *tabL = m.tabL;                                       \
+  const uint32_t tmem_base = *m.tmem_slot;                                    \
+  const int D = tb.D;                                                         \
+  (void)full; (void)empty; (void)tmem_full; (void)tmem_empty; (void)sig_full; \
+  (void)prod_bar; (void)gbar; (void)rowG; (void)rowD2; (void)rowSig;          \
+  (void)tabS; (void)tabH; (void)tabL; (void)tmem_base; (void)D; (void)stages; \
+  (void)warp;
+
+template <int kMode>
+__device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, RoleState& rs) {
+  CUROB_ROLE_PROLOGUE
     // ------------------------------------------------------------ producers
     // Thread = candidate row r.  The raw x values of a K stage are gathered
     // with 4-byte cp.async straight into the stage's own A area (row r only:
@@ -416,16 +491,18 @@ __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
     // overwrites that row of every part, so no other thread is involved.
     const int r = warp * 32 + lane;
     const long long grow = row0 + r;
-    const bool vrow = grow < args.N;
-    const float* xrow = args.x + (vrow ? grow : 0) * (long long)D;
-    const int P = args.nstage - 1;  // gather prefetch depth (stages)
-    uint32_t it = 0, pphase = 0;
+    const bool vrow = grow < a.N;
+    const float* xrow = a.x + (vrow ? grow : 0) * (long long)D;
+    const int P = a.nstage - 1;  // gather prefetch depth (stages)
+    uint32_t& it = rs.it;
+    uint32_t& pphase = rs.pphase;
     bool ok = true;
-    for (int ci = 0; ci < F.ncomp && ok; ++ci) {
+    for (int ci = 0; ci < F.ncomp && ok; ++ci, ++rs.comp_it) {
+      const uint32_t cg = rs.comp_it;  // component counter across tiles
       const Component Cm = tb.comp[F.comp0 + ci];
       const int* S = tb.S + Cm.base;
-      const float* ohi = args.ohi + Cm.base;
-      const float* olo = args.olo + Cm.base;
+      const float* ohi = a.ohi + Cm.base;
+      const float* olo = a.olo + Cm.base;
       double d2 = 0.0;
       float isig = 1.f;
       if constexpr (kMode == M_EXACT) {
@@ -433,7 +510,7 @@ __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
         // read in natural order (contiguous row, o as FP32)
         float mx = 0.f;
         if (vrow) {
-          const float* on = args.onat + Cm.base;
+          const float* on = a.onat + Cm.base;
           int k = 0;
           if ((D & 3) == 0) {
             const float4* x4 = reinterpret_cast<const float4*>(xrow);
@@ -451,9 +528,9 @@ __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
         int e = 0;
         if (mx > 0.f && mx < 3.0e38f) e = ilogbf(mx * 1.0009765625f) + 1;
         isig = ldexpf(1.f, -e);
-        rowSig[(ci % kSigRing) * kTileM + r] = ldexpf(1.f, e);
+        rowSig[(cg % kSigRing) * kTileM + r] = ldexpf(1.f, e);
         __syncwarp();
-        if (lane == 0) mbar_arrive(&sig_full[ci % kSigRing]);
+        if (lane == 0) mbar_arrive(&sig_full[cg % kSigRing]);
       }
       for (int si = 0; si < Cm.nseg && ok; ++si) {
         const Segment sg = tb.seg[Cm.seg0 + si];
@@ -477,10 +554,10 @@ __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
         // thread's copies arrive on gbar[stage] when they land.
         auto issue = [&](int q) -> bool {
           const uint32_t g = it0 + (uint32_t)q;
-          const int stage = g % args.nstage;
-          if (!mbar_wait(&empty[stage], ((g / args.nstage) & 1u) ^ 1u, abort_flag, tb.status))
+          const int stage = g % a.nstage;
+          if (!mbar_wait(&empty[stage], ((g / a.nstage) & 1u) ^ 1u, abort_flag, tb.status))
             return false;
-          uint8_t* A = stages + (size_t)stage * args.stage_bytes;
+          uint8_t* A = stages + (size_t)stage * a.stage_bytes;
           const int t = q % nslab;
           constexpr int kRowsPerInst = 32 / kKs;            // 2 (TF32) or 1
           const int k = lane % kKs;                         // column of the stage
@@ -492,8 +569,8 @@ __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
           for (int i = 0; i < 32 / kRowsPerInst; ++i) {
             const int rr = warp * 32 + i * kRowsPerInst + lane / kKs;
             const long long gr = row0 + rr;
-            const bool in = cin && gr < args.N;
-            const float* src = in ? args.x + gr * (long long)D + col : args.x;
+            const bool in = cin && gr < a.N;
+            const float* src = in ? a.x + gr * (long long)D + col : a.x;
             const uint32_t dst = smem_u32(A + rr * kRowBytes) + dcol;
             asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src),
                          "r"(in ? 4 : 0)
@@ -507,12 +584,12 @@ __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
         const int npre = min(P, total);
         for (int q = 0; q < npre && ok; ++q) ok = issue(q);
         for (int q = 0; q < total && ok; ++q, ++it) {
-          if (!mbar_wait(&gbar[it % args.nstage], (it / args.nstage) & 1u, abort_flag, tb.status)) {
+          if (!mbar_wait(&gbar[it % a.nstage], (it / a.nstage) & 1u, abort_flag, tb.status)) {
             ok = false;
             break;
           }
-          const int stage = it % args.nstage;
-          uint8_t* A = stages + (size_t)stage * args.stage_bytes;
+          const int stage = it % a.nstage;
+          uint8_t* A = stages + (size_t)stage * a.stage_bytes;
           const int t = q % nslab;
           float yh[kKs], yl[kKs];
 #pragma unroll
@@ -603,21 +680,27 @@ __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
       }
       rowD2[ci * kTileM + r] = d2;
     }
-  } else if (warp < 8) {
+}
+
+template <int kMode>
+__device__ void epilogue_tile(const MmaArgs& a, const Smem& m, long long row0, RoleState& rs) {
+  CUROB_ROLE_PROLOGUE
+  (void)row0;
     // ------------------------------------------------------------- epilogue
     const int q = warp - 4;                 // TMEM lane quadrant
     const int r = q * 32 + lane;            // candidate row in the tile
     const uint32_t t_lane = tmem_base + ((uint32_t)(q * 32) << 16);
-    uint32_t chunk_it = 0;
+    uint32_t& chunk_it = rs.chunk_it;
     EpiState st;
-    for (int ci = 0; ci < F.ncomp && !*abort_flag; ++ci) {
+    for (int ci = 0; ci < F.ncomp && !*abort_flag; ++ci, ++rs.comp_it) {
+      const uint32_t cg = rs.comp_it;
       const Component Cm = tb.comp[F.comp0 + ci];
       double gsum = 0.0;
       float sig = 1.f;
       if constexpr (kMode == M_EXACT) {
-        if (!mbar_wait(&sig_full[ci % kSigRing], (ci / kSigRing) & 1u, abort_flag, tb.status))
+        if (!mbar_wait(&sig_full[cg % kSigRing], (cg / kSigRing) & 1u, abort_flag, tb.status))
           break;
-        sig = rowSig[(ci % kSigRing) * kTileM + r];
+        sig = rowSig[(cg % kSigRing) * kTileM + r];
       }
       bool ok = true;
       for (int si = 0; si < Cm.nseg && ok; ++si) {
@@ -631,7 +714,7 @@ __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
         es.aux = sg.aux_off >= 0 ? tb.aux32 + sg.aux_off : nullptr;
         es.gpos = sg.gpos;
         es.gfirst = sg.gfirst;
-        const float* tau = args.tau + sg.tau_off;
+        const float* tau = a.tau + sg.tau_off;
         if (sg.gfirst) st.open();
         const int nchunk = kMode == M_EXACT ? (sg.npad + kExactNC - 1) / kExactNC : 1;
         for (int cc = 0; cc < nchunk; ++cc, ++chunk_it) {
@@ -673,10 +756,16 @@ __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
       if (!ok) break;
       rowG[ci * kTileM + r] = gsum;
     }
-  } else if (warp == 8) {
+}
+
+template <int kMode>
+__device__ void mma_tile(const MmaArgs& a, const Smem& m, long long row0, RoleState& rs) {
+  CUROB_ROLE_PROLOGUE
+  (void)row0;
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
-      uint32_t it = 0, chunk_it = 0;
+      uint32_t& it = rs.it;
+      uint32_t& chunk_it = rs.chunk_it;
       bool ok = true;
       for (int ci = 0; ci < F.ncomp && ok && !*abort_flag; ++ci) {
         const Component Cm = tb.comp[F.comp0 + ci];
@@ -696,14 +785,14 @@ __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
             }
             tc_fence_after();
             for (int t = 0; t < nslab; ++t, ++it) {
-              const int stage = it % args.nstage;
-              const uint32_t ph = (it / args.nstage) & 1u;
+              const int stage = it % a.nstage;
+              const uint32_t ph = (it / a.nstage) & 1u;
               if (!mbar_wait(&full[stage], ph, abort_flag, tb.status)) {
                 ok = false;
                 break;
               }
               tc_fence_after();
-              const uint32_t sa = smem_u32(stages + (size_t)stage * args.stage_bytes);
+              const uint32_t sa = smem_u32(stages + (size_t)stage * a.stage_bytes);
               const uint32_t sb = sa + kParts * kPartBytes;
               const uint32_t bpart = (uint32_t)(nc * kRowBytes);
 #pragma unroll
@@ -716,10 +805,10 @@ __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
                   for (int w = 0; w < 4; ++w) {
                     const uint32_t dt = tmem_base + (uint32_t)(w * kExactNC);
 #pragma unroll
-                    for (int a = 0; a <= w; ++a) {
-                      const uint64_t da = sdesc_sw64(sa + a * kPartBytes + ko);
-                      const uint64_t db = sdesc_sw64(sb + (w - a) * bpart + ko);
-                      tc_mma<false>(dt, da, db, id0, (a == 0) ? first : 1u);
+                    for (int ia = 0; ia <= w; ++ia) {
+                      const uint64_t da = sdesc_sw64(sa + ia * kPartBytes + ko);
+                      const uint64_t db = sdesc_sw64(sb + (w - ia) * bpart + ko);
+                      tc_mma<false>(dt, da, db, id0, (ia == 0) ? first : 1u);
                     }
                   }
                 } else {
@@ -743,10 +832,15 @@ __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
       }
     }
     __syncwarp();
-  } else {
+}
+
+template <int kMode>
+__device__ void loader_tile(const MmaArgs& a, const Smem& m, long long row0, RoleState& rs) {
+  CUROB_ROLE_PROLOGUE
+  (void)row0;
     // ------------------------------------------------------------- B loads
     if (lane == 0) {
-      uint32_t it = 0;
+      uint32_t& it = rs.it;
       bool ok = true;
       for (int ci = 0; ci < F.ncomp && ok && !*abort_flag; ++ci) {
         const Component Cm = tb.comp[F.comp0 + ci];
@@ -755,19 +849,19 @@ __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
           const int nslab = sg.npad / kKs;
           const int nchunk = kMode == M_EXACT ? (sg.npad + kExactNC - 1) / kExactNC : 1;
           const long long fl = image_floats(sg.npad);
-          const uint8_t* base = args.img + ((size_t)sg.img_off + (size_t)kMode * fl) * 4;
+          const uint8_t* base = a.img + ((size_t)sg.img_off + (size_t)kMode * fl) * 4;
           for (int cc = 0; cc < nchunk && ok; ++cc) {
             const int nc = kMode == M_EXACT ? min(kExactNC, sg.npad - cc * kExactNC) : sg.npad;
             const uint32_t bytes = (uint32_t)(kParts * nc * kRowBytes);
             const uint8_t* src = base + (size_t)cc * nslab * kParts * kExactNC * kRowBytes;
             for (int t = 0; t < nslab; ++t, ++it) {
-              const int stage = it % args.nstage;
-              const uint32_t ph = (it / args.nstage) & 1u;
+              const int stage = it % a.nstage;
+              const uint32_t ph = (it / a.nstage) & 1u;
               if (!mbar_wait(&empty[stage], ph ^ 1u, abort_flag, tb.status)) {
                 ok = false;
                 break;
               }
-              uint8_t* dst = stages + (size_t)stage * args.stage_bytes + kParts * kPartBytes;
+              uint8_t* dst = stages + (size_t)stage * a.stage_bytes + kParts * kPartBytes;
               mbar_arrive_expect_tx(&full[stage], bytes);
               bulk_g2s(dst, src + (size_t)t * bytes, bytes, &full[stage]);
             }
@@ -776,35 +870,55 @@ __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
       }
     }
     __syncwarp();
-  }
+}
 
-  // drain: every issued MMA has been consumed by the epilogue (or the CTA
-  // aborted); write f, free TMEM.
+template <int kMode>
+__device__ inline void run_tile(const MmaArgs& a, const Smem& m, long long row0, RoleState& rs) {
+  const int warp = threadIdx.x >> 5;
+  if (warp < 4) producer_tile<kMode>(a, m, row0, rs);
+  else if (warp < 8) epilogue_tile<kMode>(a, m, row0, rs);
+  else if (warp == 8) mma_tile<kMode>(a, m, row0, rs);
+  else loader_tile<kMode>(a, m, row0, rs);
+  // every issued MMA has been consumed by the epilogue (or the CTA aborted)
   tc_fence_before();
   __syncthreads();
-  if (warp >= 4 && warp < 8 && !*abort_flag) {
-    const int r = (warp - 4) * 32 + lane;
-    const long long grow = row0 + r;
-    if (grow < args.N) {
-      double f;
-      if (F.composition) {
-        double G[kMaxComponents], d2v[kMaxComponents];
-        for (int ci = 0; ci < F.ncomp; ++ci) {
-          G[ci] = rowG[ci * kTileM + r];
-          d2v[ci] = rowD2[ci * kTileM + r];
-        }
-        f = compose(tb.comp + F.comp0, F.ncomp, G, d2v, D);
-      } else {
-        f = rowG[r];
-      }
-      args.out[grow] = (float)(f + kFopt);
-    }
+  tc_fence_after();
+  write_outputs(a, m, row0);
+}
+
+// One launch per function: CTA b evaluates candidates [128 b, 128 b + 128).
+template <int kMode>
+__global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  const Smem m = smem_map(smem_raw, args.nstage, args.stage_bytes);
+  cta_setup(m, args.nstage);
+  RoleState rs;
+  run_tile<kMode>(args, m, (long long)blockIdx.x * kTileM, rs);
+  cta_teardown(m);
+}
+
+// Persistent launch over a ragged batch: each CTA takes work items (an
+// instance and one of its 128-candidate tiles) from a global counter until
+// none is left; barrier phases carry over from item to item.  The counter
+// must be 0 at launch.
+template <int kMode>
+__global__ void __launch_bounds__(kThreads, 1)
+mma_batch_kernel(const MmaArgs* __restrict__ insts, const int2* __restrict__ work, int nwork,
+                 int* counter, int nstage, int stage_bytes) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  const Smem m = smem_map(smem_raw, nstage, stage_bytes);
+  cta_setup(m, nstage);
+  RoleState rs;
+  for (;;) {
+    if (threadIdx.x == 0) *m.item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int w = *m.item;
+    if (w >= nwork || *m.abort_flag) break;
+    const int2 W = work[w];
+    run_tile<kMode>(insts[W.x], m, (long long)W.y * kTileM, rs);
+    __syncthreads();  // outputs written; per-row tables free for the next item
   }
-  if (warp == 8) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
-                 "r"(kMaxNpad));
-  }
+  cta_teardown(m);
 }
 
 // ----------------------------------------------------- operand image builder
@@ -902,7 +1016,7 @@ template <int kMode>
 size_t stage_bytes_for(int ncmax) {
   return (size_t)MC<kMode>::kParts * kPartBytes + (size_t)MC<kMode>::kParts * ncmax * kRowBytes;
 }
-size_t ctrl_bytes() {  // barriers (<= 256 B) + per-row tables + block table
+size_t ctrl_bytes() {  // barriers and work item (<= 256 B) + per-row tables + block table
   return 256 + 2 * sizeof(double) * kMaxComponents * kTileM + sizeof(float) * kSigRing * kTileM +
          3 * sizeof(float) * kMaxNpad;
 }
@@ -1044,6 +1158,57 @@ int mma_auto_mode(const MmaPlan& p, const Function& F) {
   (void)p;
   return F.sensitive ? CUROB_PRECISION_EXACT : CUROB_PRECISION_TF32X3;
 }
+
+namespace {
+// Stage geometry of the EXACT persistent kernel (independent of the item).
+struct BatchGeom {
+  int nstage, stage_bytes;
+  size_t smem;
+};
+BatchGeom batch_geom() {
+  BatchGeom g;
+  const size_t sb = stage_bytes_for<M_EXACT>(kExactNC);
+  g.stage_bytes = (int)sb;
+  g.nstage = (int)std::min<size_t>(4, (219 * 1024 - ctrl_bytes()) / sb);
+  g.smem = g.nstage * sb + ctrl_bytes() + 1024;
+  return g;
+}
+}  // namespace
+
+size_t mma_args_bytes() { return sizeof(MmaArgs); }
+
+void mma_fill_args(void* dst, const MmaPlan& p, const Tables& tb, const Function& F,
+                   const float* x, float* out, int N) {
+  const BatchGeom g = batch_geom();
+  MmaArgs a;
+  a.tb = tb;
+  a.F = F;
+  a.x = x;
+  a.out = out;
+  a.N = N;
+  a.ohi = p.ohi;
+  a.olo = p.olo;
+  a.img = reinterpret_cast<const uint8_t*>(p.img);
+  a.tau = p.tau;
+  a.onat = p.onat;
+  a.nstage = g.nstage;
+  a.stage_bytes = g.stage_bytes;
+  memcpy(dst, &a, sizeof(a));
+}
+
+cudaError_t launch_mma_batch(const void* d_args, const int2* d_work, int nwork, int* d_counter,
+                             int grid, cudaStream_t st) {
+  const BatchGeom g = batch_geom();
+  cudaError_t e = cudaFuncSetAttribute(mma_batch_kernel<M_EXACT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+  if (e != cudaSuccess) return e;
+  mma_batch_kernel<M_EXACT><<<grid, kThreads, g.smem, st>>>(
+      reinterpret_cast<const MmaArgs*>(d_args), d_work, nwork, d_counter, g.nstage,
+      g.stage_bytes);
+  return cudaGetLastError();
+}
+
+int mma_max_block() { return kMaxNpad; }
 
 cudaError_t launch_mma(const MmaPlan& p, const Tables& tb, const Function& F, int mode,
                        const float* x, int N, float* out, cudaStream_t st) {

@@ -34,4 +34,16 @@ int mma_auto_mode(const MmaPlan& p, const Function& F);
 cudaError_t launch_mma(const MmaPlan& p, const Tables& tb, const Function& F, int mode,
                        const float* x, int N, float* out, cudaStream_t st);
 
+// Persistent EXACT-mode launches over a ragged batch.
+size_t mma_args_bytes();
+// Writes the device-side argument block of one batch item into dst (host).
+void mma_fill_args(void* dst, const MmaPlan& p, const Tables& tb, const Function& F,
+                   const float* x, float* out, int N);
+// Launches the persistent kernel on `grid` CTAs over nwork (item, tile)
+// pairs; *d_counter must be 0.
+cudaError_t launch_mma_batch(const void* d_args, const int2* d_work, int nwork, int* d_counter,
+                             int grid, cudaStream_t st);
+// Largest block width the tensor-core kernels take.
+int mma_max_block();
+
 }  // namespace curob

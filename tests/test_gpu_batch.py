@@ -1,0 +1,109 @@
+"""Ragged batches: 64 (function, D, population) items, one persistent
+tensor-core launch captured in a CUDA graph, checked item by item against the
+FP64 oracle and bit for bit against one launch per item."""
+import numpy as np
+import pytest
+
+import gpu_util as gu
+from paper_1407_7737_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    gu.invalidate()
+    return torch
+
+
+def _batch_inputs(torch, n_items, seed, nmax=8192):
+    items = inputs.ragged_instances(n_items, seed, nmax=nmax)
+    xs, outs, specs = [], [], []
+    for i, (fid, D, N) in enumerate(items):
+        s = 1000 + D  # one instance per dimension
+        x = inputs.uniform(N, D, 50 + i).astype(np.float32)
+        xs.append(x)
+        outs.append(torch.empty(N, dtype=torch.float32, device="cuda"))
+        specs.append((fid, D, s, N))
+    dev = [torch.from_numpy(x).cuda() for x in xs]
+    return specs, xs, dev, outs
+
+
+def test_ragged_batch_matches_oracle_and_separate(orc, torch_cuda):
+    torch = torch_cuda
+    cu = gu.cu()
+    specs, xs, dev, outs = _batch_inputs(torch, 64, 7)
+    b = cu.curob_batch_create([(f, D, s, N, x, o) for (f, D, s, N), x, o in zip(specs, dev, outs)])
+    try:
+        cu.curob_batch_run(b)
+        cu.curob_batch_status(b)
+        first = [o.clone() for o in outs]
+        cu.curob_batch_run(b)  # graph replay
+        cu.curob_batch_status(b)
+        for a, c in zip(first, outs):
+            assert torch.equal(a, c)
+        nwork, grid, order = cu.curob_batch_schedule(b)
+        assert nwork == sum((N + 127) // 128 for (_, _, _, N) in specs)
+        assert 1 <= grid <= torch.cuda.get_device_properties(0).multi_processor_count
+        assert order in (0, 1, 2)
+        for o in outs:
+            o.fill_(float("nan"))
+        cu.curob_batch_run_separate(b)
+        cu.curob_batch_status(b)
+        for a, c in zip(first, outs):
+            assert torch.equal(a, c)  # same tile arithmetic, bit for bit
+        rng = np.random.default_rng(0)
+        bad = []
+        for (fid, D, s, N), x, o in zip(specs, xs, first):
+            got = o.cpu().numpy().astype(np.float64)
+            rows = np.arange(N) if N * D <= 200_000 else np.unique(
+                np.r_[0, N - 1, rng.integers(0, N, 24)])
+            ok, worst, excused, raw = gu.fp32_check(orc, fid, D, s, x, got, rows)
+            if not ok:
+                bad.append((fid, D, N, raw))
+        assert not bad, bad
+    finally:
+        cu.curob_batch_destroy(b)
+
+
+def test_batch_argument_errors(torch_cuda):
+    torch = torch_cuda
+    cu = gu.cu()
+    x = torch.zeros(4, 10, device="cuda")
+    o = torch.zeros(4, device="cuda")
+    C = cu.CODES
+    for item, code in [((40, 10, 0, 4, x, o), "CUROB_ERR_INVALID_FID"),
+                       ((23, 9, 0, 4, x, o), "CUROB_ERR_INVALID_DIM"),
+                       ((0, 10, 0, -1, x, o), "CUROB_ERR_INVALID_ARGUMENT"),
+                       ((0, 2000, 0, 4, x, o), "CUROB_ERR_UNSUPPORTED")]:
+        with pytest.raises(cu.CurobError) as e:
+            cu.curob_batch_create([item])
+        assert e.value.code == C[code]
+    host = np.zeros((4, 10), dtype=np.float32)
+    with pytest.raises(cu.CurobError) as e:
+        cu.curob_batch_create([(0, 10, 0, 4, host, o)])
+    assert e.value.code == C["CUROB_ERR_INVALID_ARGUMENT"]
+
+
+def test_batch_with_empty_and_single_rows(orc, torch_cuda):
+    torch = torch_cuda
+    cu = gu.cu()
+    specs = [(0, 10, 3, 0), (8, 30, 3, 1), (29, 50, 3, 129), (36, 100, 3, 127)]
+    xs = [inputs.uniform(max(N, 1), D, 9)[:N].astype(np.float32) for (_, D, _, N) in specs]
+    dev = [torch.from_numpy(x).cuda() if x.size else torch.zeros(1, device="cuda") for x in xs]
+    outs = [torch.empty(max(N, 1), device="cuda") for (_, _, _, N) in specs]
+    b = cu.curob_batch_create([(f, D, s, N, x, o) for (f, D, s, N), x, o in zip(specs, dev, outs)])
+    try:
+        cu.curob_batch_run(b)
+        cu.curob_batch_status(b)
+        for (fid, D, s, N), x, o in zip(specs, xs, outs):
+            if N == 0:
+                continue
+            got = o[:N].cpu().numpy().astype(np.float64)
+            ok, *_ = gu.fp32_check(orc, fid, D, s, x, got)
+            assert ok, (fid, D, N)
+    finally:
+        cu.curob_batch_destroy(b)
