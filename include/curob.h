@@ -148,6 +148,26 @@ curob_status curob_set_component(int fid, int comp, const double* o, const int* 
  * Sec. 6: the member with the smallest bias).  Host pointer, D doubles. */
 curob_status curob_get_optimum(int fid, double* xopt);
 
+/* Evaluates n_items functions of the current instance (curob_initialize) on
+ * FP32 candidates in one persistent tensor-core launch, WITHOUT ALLOCATING
+ * anything: for callers that may not allocate device memory once they are
+ * running, e.g. an optimizer that reserves its whole GPU budget at start-up,
+ * or a plugin whose host framework owns every device allocation.  The paper
+ * has no counterpart; this is a variant of the ragged-batch launch whose
+ * work list, argument blocks and work counter live in a 160 KB static device
+ * array that every GPU loading the library holds until the process exits.
+ * fids[i], x[i] (device, N[i] x D), N[i], out[i] (device, N[i]) describe item
+ * i; all host arrays.  Every item uses the EXACT contraction (same values as
+ * curob_evaluatef with CUROB_PRECISION_EXACT).  Limits: at most 64 items and
+ * 16384 tiles of 128 candidates per call (CUROB_ERR_CAPACITY beyond), each
+ * N[i] <= max_concurrency, block widths <= 512 (else UNSUPPORTED).  The
+ * first call on a device looks the array's address up.  All calls share the
+ * array and each call overwrites it: calls that overlap on the GPU (two
+ * streams, two threads) race; order them on one stream.  Asynchronous on
+ * `stream`. */
+curob_status curob_evaluatef_multi_noalloc(const int* fids, const float* const* x, const int* N,
+                                           float* const* out, int n_items, curob_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * Ragged batches (this library's extension; the paper evaluates one function
  * at one D at a time).  A batch is a list of (function, D, seed, population)

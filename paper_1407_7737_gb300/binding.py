@@ -50,6 +50,7 @@ _SIGS = [
     ("curob_batch_schedule", _I, [_P, _P, _P, _P]),
     ("curob_batch_status", _I, [_P, _P]),
     ("curob_batch_destroy", _I, [_P]),
+    ("curob_evaluatef_multi_noalloc", _I, [_P, _P, _P, _P, _I, _P]),
 ]
 EXPORTS = [s[0] for s in _SIGS]
 
@@ -251,6 +252,18 @@ def curob_batch_status(batch, stream=None, check=True):
 
 def curob_batch_destroy(batch, check=True):
     return _call("curob_batch_destroy", batch, check=check)
+
+
+def curob_evaluatef_multi_noalloc(fids, xs, Ns, outs, stream=None, check=True):
+    """Several functions of the current instance in one launch that allocates
+    no device memory; xs / outs are device tensors or pointers."""
+    n = len(fids)
+    f = (ctypes.c_int * n)(*fids)
+    nn = (ctypes.c_int * n)(*Ns)
+    xp = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+    op = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
+    return _call("curob_evaluatef_multi_noalloc", ctypes.addressof(f), ctypes.addressof(xp),
+                 ctypes.addressof(nn), ctypes.addressof(op), n, _stream(stream), check=check)
 
 
 # ----- tensor conveniences ---------------------------------------------------

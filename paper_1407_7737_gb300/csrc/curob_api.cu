@@ -274,3 +274,100 @@ curob_status curob_get_optimum(int fid, double* xopt) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free evaluation of several functions in one launch.
+//
+// For callers that may not allocate device memory at evaluation time: code
+// that reserves all of its GPU memory up front under a fixed budget (an
+// optimizer embedded in a real-time or safety-constrained loop), or a plugin
+// whose host framework owns every device allocation.  The work list, the
+// per-function argument blocks and the work counter of the persistent kernel
+// live in this file's static device array instead of cudaMalloc'd memory; the
+// caller passes candidates and outputs, and the instance is the one
+// curob_initialize built.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kNoAllocMaxItems = 64;       // functions per call
+constexpr int kNoAllocMaxTiles = 16384;    // 128-candidate tiles per call
+constexpr size_t kNoAllocArgsBytes = 64 * 512;
+constexpr size_t kNoAllocWorkOff = 256 + kNoAllocArgsBytes;
+constexpr size_t kNoAllocBytes = kNoAllocWorkOff + kNoAllocMaxTiles * sizeof(int2);
+constexpr int kNoAllocMaxDevices = 64;
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};        // device address of the array, per device
+unsigned char g_noalloc_args[kNoAllocArgsBytes];      // host staging (no host allocation either)
+int2 g_noalloc_work[kNoAllocMaxTiles];
+}  // namespace
+
+// 160 KB on every device that loads the library, held until the process exits.
+// Layout: [work counter | 256 B][argument blocks | 32 KB][work list | 128 KB].
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+extern "C" curob_status curob_evaluatef_multi_noalloc(const int* fids, const float* const* x,
+                                                      const int* N, float* const* out,
+                                                      int n_items, curob_stream_t stream) {
+  using namespace curob;
+  if (!g.init) return CUROB_ERR_NOT_INITIALIZED;
+  if (!fids || !x || !N || !out) return CUROB_ERR_NULL_POINTER;
+  if (n_items < 1) return CUROB_ERR_INVALID_ARGUMENT;
+  if (n_items > kNoAllocMaxItems) return CUROB_ERR_CAPACITY;
+  if (mma_args_bytes() * (size_t)n_items > kNoAllocArgsBytes) return CUROB_ERR_CAPACITY;
+  long long tiles = 0;
+  for (int i = 0; i < n_items; ++i) {
+    const int fid = fids[i];
+    if (fid < 0 || fid >= kNumFunctions) return CUROB_ERR_INVALID_FID;
+    if (!g.inst.func_ok[fid]) return CUROB_ERR_INVALID_DIM;
+    if (N[i] < 0) return CUROB_ERR_INVALID_ARGUMENT;
+    if (N[i] > g.max_conc) return CUROB_ERR_CAPACITY;
+    if (!mma_supports(g.inst.mma, g.inst.func[fid])) return CUROB_ERR_UNSUPPORTED;
+    if (N[i] > 0) {
+      if (!x[i] || !out[i]) return CUROB_ERR_NULL_POINTER;
+      if (!device_accessible(x[i]) || !device_accessible(out[i]))
+        return CUROB_ERR_INVALID_ARGUMENT;
+    }
+    tiles += (N[i] + 127) / 128;
+  }
+  if (tiles > kNoAllocMaxTiles) return CUROB_ERR_CAPACITY;
+  if (tiles == 0) return CUROB_OK;
+
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices)
+    return CUROB_ERR_CUDA;
+  if (!g_noalloc_addr[dev]) {  // first call on this device: look the array up once
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return CUROB_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  unsigned char* base = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  const size_t ab = mma_args_bytes();
+  int nwork = 0;
+  for (int i = 0; i < n_items; ++i) {
+    mma_fill_args(g_noalloc_args + ab * i, g.inst.mma, g.inst.tables(), g.inst.func[fids[i]],
+                  x[i], out[i], N[i]);
+  }
+  // round robin over the functions, so every CTA sees a mix of them
+  for (int t = 0; nwork < tiles; ++t)
+    for (int i = 0; i < n_items; ++i)
+      if (t < (N[i] + 127) / 128) g_noalloc_work[nwork++] = make_int2(i, t);
+  cudaStream_t st = (cudaStream_t)stream;
+  // the counter must start at 0; the rest is overwritten before use
+  if (cudaMemsetAsync(base, 0, sizeof(int), st) != cudaSuccess ||
+      cudaMemcpyAsync(base + 256, g_noalloc_args, ab * n_items, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(base + kNoAllocWorkOff, g_noalloc_work, sizeof(int2) * nwork,
+                      cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return CUROB_ERR_CUDA;
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::max(1, std::min(nsm, nwork));
+  if (launch_mma_batch(base + 256, reinterpret_cast<const int2*>(base + kNoAllocWorkOff), nwork,
+                       reinterpret_cast<int*>(base), grid, st) != cudaSuccess)
+    return CUROB_ERR_CUDA;
+  return CUROB_OK;
+}
