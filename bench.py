@@ -48,6 +48,12 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the FP64 and forced-precision side measurements")
+    ap.add_argument("--no-surrogate", action="store_true",
+                    help="skip the learned pre-screen side measurement")
+    ap.add_argument("--surrogate-fids", default="all",
+                    help="functions of the learned pre-screen measurement (all, or a,b,c)")
+    ap.add_argument("--surrogate-n", type=int, default=1_000_000,
+                    help="training samples and pool size of the pre-screen measurement")
     ap.add_argument("--profile-fid", type=int, default=None,
                     help="profiling case: two launches of one function, no JSON")
     return ap.parse_args()
@@ -268,31 +274,45 @@ def run_curob(args):
     if rank == 0 and not args.no_extra:
         ragged = ragged_batch(cu, torch, dev, stream, reps=max(3, args.steps))
 
-    # roofline of the dominant kernel (the path holding most of the step)
+    # roofline of the dominant kernel (the tensor-core mode holding most of
+    # the step).  Its algorithmic work is 2 sum_b n_b^2 flops per candidate
+    # and rotated component; the peak is the rate of algorithmic products
+    # that mode can reach: TF32X3 runs 3 TF32 products per product, EXACT 10
+    # BF16 products, BF16X3 3 BF16 products.
     pk, src = peaks()
     flops = np.array([algorithmic_flops(cu, f) * N for f in range(NFUN)], dtype=np.float64)
-    mma = np.array([m in (1, 2, 4) for m in modes])
-    t_mma, t_simt = launch_ms[mma].sum(), launch_ms[~mma].sum()
-    if t_mma >= t_simt:
-        sel = mma & (flops > 0)
-        achieved = flops[sel].sum() / (launch_ms[sel].sum() / 1e3) / 1e12
-        peak = pk["bf16_tflops"] * (1.1 / 2.25)  # TF32 dense = bf16 x nominal ratio
-        roof = {"bound": "tensor", "kernel": "mma_eval_kernel (tcgen05 TF32x3)",
-                "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_source": f"{src} bf16 x 1.1/2.25 (TF32/BF16 nominal ratio)",
-                "share_of_step": round(t_mma / launch_ms.sum(), 3),
-                "note": "algorithmic flops 2*sum(n_b^2) per candidate; three split products execute 3x"}
-    else:
-        sel = (~mma) & (flops > 0)
-        achieved = flops[sel].sum() / (launch_ms[sel].sum() / 1e3) / 1e12
-        peak = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 FMA lanes x 2 flop x max SM clock
-        roof = {"bound": "alu", "kernel": "eval_simt_f32_kernel (compensated FP32)",
-                "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                "share_of_step": round(t_simt / launch_ms.sum(), 3),
-                "note": "algorithmic flops 2*sum(n_b^2) per candidate; the compensated dot product executes ~6x"}
+    modes_a = np.array(modes)
+    bf16 = pk["bf16_tflops"]
+    mode_info = {
+        1: ("mma_eval_kernel<TF32X3>", bf16 * (1.1 / 2.25) / 3.0,
+            f"{src} bf16 burst x 1.1/2.25 (TF32/BF16 nominal ratio) / 3 TF32 products"),
+        2: ("mma_eval_kernel<BF16X3>", bf16 / 3.0, f"{src} bf16 burst / 3 BF16 products"),
+        4: ("mma_eval_kernel<EXACT>", bf16 / 10.0, f"{src} bf16 burst / 10 BF16 products"),
+        3: ("eval_simt_f32_kernel", 152 * 128 * 2 * 2.07e9 / 1e12 / 6.0,
+            "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz / ~6 ops per compensated product"),
+    }
+    share = {m: launch_ms[modes_a == m].sum() for m in set(modes)}
+    dom = max(share, key=share.get)
+    sel = (modes_a == dom) & (flops > 0)
+    achieved = flops[sel].sum() / (launch_ms[sel].sum() / 1e3) / 1e12
+    kname, peak, psrc = mode_info[dom]
+    roof = {"bound": "tensor" if dom != 3 else "alu", "kernel": kname,
+            "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "peak_source": psrc, "share_of_step": round(share[dom] / launch_ms.sum(), 3),
+            "launches_per_step": int(sel.sum()),
+            "note": "achieved = algorithmic flops (2*sum n_b^2 per candidate and rotated "
+                    "component) / CUDA-event time of those launches"}
+    # per function: time against the tensor bound of its own mode and the
+    # HBM bound of reading x once (4 D + 4 bytes per candidate)
+    per_fn = []
+    for f in range(NFUN):
+        pkm = mode_info[modes[f]][1]
+        t_tc = flops[f] / (pkm * 1e12) * 1e3
+        t_hbm = (4.0 * D + 4.0) * N / (pk["hbm_gbs"] * 1e9) * 1e3
+        per_fn.append({"fid": f, "ms": round(float(launch_ms[f]), 4),
+                       "tensor_bound_ms": round(t_tc, 4), "hbm_bound_ms": round(t_hbm, 4),
+                       "frac_of_binding": round(max(t_tc, t_hbm) / float(launch_ms[f]), 4)})
 
     e2e = None
     if not args.no_e2e:
@@ -316,6 +336,12 @@ def run_curob(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(sample_n=8)
 
+    surrogate = None
+    if rank == 0 and not args.no_surrogate:
+        cu.curob_dispose()
+        surrogate = surrogate_bench(cu, torch, dev, stream, args)
+        cu.curob_initialize(D, N, SEED)
+
     gpu_launches = NFUN * args.steps
     if rank == 0:
         line = {
@@ -332,13 +358,119 @@ def run_curob(args):
             "per_function_ms": [round(v, 4) for v in launch_ms.tolist()],
             "per_function_path": [{1: "tf32x3", 2: "bf16x3", 3: "simt", 4: "exact"}[m]
                                   for m in modes],
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "ragged_batch": ragged,
-            "clocks": clk.summary(), "gpu_launches": gpu_launches,
+            "roofline": roof, "roofline_per_function": per_fn, "cpu_baseline": cpu, "e2e": e2e, "ragged_batch": ragged,
+            "surrogate": surrogate, "clocks": clk.summary(), "gpu_launches": gpu_launches,
         }
         print(json.dumps(line))
     cu.curob_dispose()
     if pg is not None:
         pg.destroy_process_group()
+
+
+def _rank_corr(torch, a, b):
+    """Spearman's rank correlation of two device vectors (ties broken by
+    position; the values are continuous)."""
+    def ranks(v):
+        r = torch.empty_like(v, dtype=torch.float64)
+        r[torch.argsort(v)] = torch.arange(v.numel(), device=v.device, dtype=torch.float64)
+        return r - r.mean()
+    ra, rb = ranks(a), ranks(b)
+    return float((ra * rb).sum() / torch.sqrt((ra * ra).sum() * (rb * rb).sum()))
+
+
+def _mixture(torch, dev, n, xopt, seed, frac_near=0.3, sigma=10.0):
+    """n x 100 candidates: frac_near Gaussian around xopt (width sigma), the
+    rest uniform in [-100, 100]^100, rows in random order."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    x = torch.empty((n, 100), dtype=torch.float32, device=dev).uniform_(-100.0, 100.0, generator=g)
+    m = int(round(frac_near * n))
+    x[:m] = xopt[None, :] + sigma * torch.randn((m, 100), device=dev, generator=g)
+    return x[torch.randperm(n, device=dev, generator=g)].contiguous()
+
+
+def surrogate_bench(cu, torch, dev, stream, args, D_s=100, epochs=4, batch=4096, frac=0.05):
+    """Learned pre-screen at D = 100: for each function, an MLP 100-256-256-1
+    trained on n exact evaluations (70 % uniform, 30 % around x_opt with
+    sigma 10) screens a fresh pool of n candidates; the best 5 % by the
+    surrogate are evaluated exactly.  Reports the training and screening
+    throughput, Spearman's rho of prediction against exact value over the
+    pool, the regret (best exact value kept minus best in the pool) next to
+    the mean regret of a random 5 %, and the exact evaluations saved."""
+    n = args.surrogate_n
+    fids = list(range(NFUN)) if args.surrogate_fids == "all" else \
+        [int(v) for v in args.surrogate_fids.split(",")]
+    k = int(n * frac)
+    cu.curob_initialize(D_s, n, SEED)
+    s = cu.curob_surrogate_create(batch, 7)
+    rows = []
+    t_fit = t_screen = 0.0
+    try:
+        for fid in fids:
+            xopt = torch.from_numpy(cu.curob_get_optimum(fid)).to(dev, torch.float32)
+            x = _mixture(torch, dev, n, xopt, 1000 + fid)
+            f = torch.empty(n, device=dev)
+            cu.curob_evaluatef(fid, x, n, f, stream)
+            init = cu.curob_surrogate_get_params(s) if not rows else init
+            cu.curob_surrogate_set_params(s, init)
+            steps = epochs * (n // batch)
+            hist = torch.zeros(steps, device=dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            cu.curob_surrogate_fit(s, x, f, n, 100.0, epochs, batch, 2e-3, fid, hist, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            fit_ms = e0.elapsed_time(e1)
+            del x, f
+            pool = _mixture(torch, dev, n, xopt, 5000 + fid)
+            pred = torch.empty(n, device=dev)
+            idx = torch.empty(k, dtype=torch.int32, device=dev)
+            xs = torch.empty((k, D_s), device=dev)
+            fs = torch.empty(k, device=dev)
+            cu.curob_surrogate_screen(s, fid, pool, n, k, pred, idx, xs, fs, stream)  # warm
+            torch.cuda.synchronize()
+            e0.record(stream)
+            cu.curob_surrogate_screen(s, fid, pool, n, k, pred, idx, xs, fs, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            scr_ms = e0.elapsed_time(e1)
+            cu.curob_surrogate_device_status(s, stream)
+            fpool = torch.empty(n, device=dev)
+            cu.curob_evaluatef(fid, pool, n, fpool, stream)
+            torch.cuda.synchronize()
+            best = float(fpool.min())
+            reg = float(fs.min()) - best
+            gr = torch.Generator(device=dev)
+            gr.manual_seed(fid)
+            reg_rand = float(np.mean([float(fpool[torch.randperm(n, device=dev, generator=gr)[:k]].min())
+                                      - best for _ in range(10)]))
+            h = hist.cpu().numpy()
+            per = n // batch
+            rows.append({"fid": fid, "rho": round(_rank_corr(torch, pred, fpool), 4),
+                         "regret": reg, "random_regret": reg_rand,
+                         "beats_random": reg < reg_rand,
+                         "loss_first_epoch": round(float(h[:per].mean()), 4),
+                         "loss_last_epoch": round(float(h[-per:].mean()), 4),
+                         "fit_ms": round(fit_ms, 2), "screen_ms": round(scr_ms, 3)})
+            t_fit += fit_ms
+            t_screen += scr_ms
+            del pool, pred, fpool
+    finally:
+        cu.curob_surrogate_destroy(s)
+        cu.curob_dispose()
+    rhos = [r["rho"] for r in rows]
+    return {
+        "D": D_s, "model": "MLP 100-256-256-1 GELU, BF16 operands, FP32 accumulation, AdamW",
+        "train_samples": n, "pool": n, "screened_fraction": frac, "epochs": epochs, "batch": batch,
+        "functions": len(rows),
+        "train_samples_per_s": round(epochs * (n // batch) * batch * len(rows) / (t_fit / 1e3), 1),
+        "screen_candidates_per_s": round(n * len(rows) / (t_screen / 1e3), 1),
+        "exact_evals_saved": round(1.0 / frac, 2),
+        "median_rho": float(np.median(rhos)) if rhos else None,
+        "beats_random": int(sum(r["beats_random"] for r in rows)),
+        "per_function": rows,
+    }
 
 
 def ragged_batch(cu, torch, dev, stream, reps=5, n_items=64, seed=2024):

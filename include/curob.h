@@ -51,9 +51,11 @@ typedef enum {
 /* Rotation-contraction precision of curob_evaluatef (the paper evaluates FP32
  * plainly; these are this library's choices).  TF32X3: three TF32
  * tensor-core products per term (hi*hi + hi*lo + lo*hi), FP32 accumulation.
- * BF16X3: the same with BF16 halves.  EXACT: both operands cut into four
- * 7-bit integer slices held in BF16, accumulated exactly (every partial sum
- * an integer below 2^24), z to about 2^-28 of each candidate's |x - o|_max.
+ * BF16X3: the same with BF16 halves.  EXACT: both operands cut into three
+ * integer slices held exactly in BF16; the leading slice product is
+ * accumulated exactly (every partial sum an integer below 2^23), the five
+ * lower-weight products in a second FP32 accumulator 2^-8 below it; z to
+ * about 2^-24 of each candidate's |x - o|_max, with no accumulation bias.
  * SIMT: FP32 CUDA cores with a compensated dot product.  AUTO (default):
  * EXACT for functions containing Discus, Weierstrass, expanded
  * Griewank-Rosenbrock or Katsuura (they magnify z errors), TF32X3 for the
@@ -218,6 +220,118 @@ curob_status curob_batch_status(curob_batch batch, curob_stream_t stream);
 
 /* Releases the batch (synchronises the device first). */
 curob_status curob_batch_destroy(curob_batch batch);
+
+/* ---------------------------------------------------------------------------
+ * Learned pre-screen (this library's extension; the paper has no learned
+ * part).  A surrogate is an MLP 100 -> 256 -> 256 -> 1 of one function at
+ * D = 100: u = x / 128, a1 = W1 u + b1, h1 = gelu(a1), a2 = W2 h1 + b2,
+ * h2 = gelu(a2), y = w3 . h2 + b3, gelu(a) = a Phi(a) with Phi the standard
+ * normal CDF (Hendrycks and Gimpel 2016).  It predicts t = log(f - f_opt + 1)
+ * as mu + sd * y, mu and sd the mean and standard deviation of t over its
+ * training set.  Training minimises the mean squared error of y against
+ * (t - mu) / sd with AdamW (Loshchilov and Hutter 2019: w <- w (1 - lr wd),
+ * then the bias-corrected Adam step, eps added to sqrt(v_hat)).  Weights are
+ * FP32 masters with BF16 copies; every contraction (forward and backward)
+ * runs on the tensor cores with BF16 operands (u, h1, dL/da2, dL/da1 rounded
+ * to nearest-even BF16 where they enter one) and FP32 accumulation; biases,
+ * activations outside contractions and reductions are FP32.
+ *
+ * Flat parameter vector (CUROB_SURROGATE_PARAMS floats): W1 (256 x 100,
+ * row = output unit), b1 (256), W2 (256 x 256), b2 (256), w3 (256), b3.
+ * All x, f, out, idx pointers below are DEVICE pointers unless stated;
+ * calls are asynchronous on `stream` unless stated.  Kernel-side errors
+ * (bounded waits) are reported by curob_surrogate_device_status.
+ * ------------------------------------------------------------------------- */
+#define CUROB_SURROGATE_INPUT 100
+#define CUROB_SURROGATE_HIDDEN 256
+#define CUROB_SURROGATE_PARAMS 91905
+
+typedef struct curob_surrogate_st* curob_surrogate;
+
+/* Text of the last CUDA failure recorded on the calling thread by the
+ * surrogate and selection entry points (the failing step and CUDA's error
+ * string), or "" when none.  Owned by the library. */
+const char* curob_last_error(void);
+
+/* Allocates a surrogate on the current device for training batches of up to
+ * max_batch rows (a multiple of 128, <= 2^20), initialised like PyTorch's
+ * linear layers (weights and biases uniform in +-1/sqrt(fan_in)) from a
+ * generator seeded by `seed`; mu = 0, sd = 1; AdamW lr 1e-3, betas (0.9,
+ * 0.999), eps 1e-8, weight decay 1e-4.  Errors: NULL_POINTER,
+ * INVALID_ARGUMENT, UNSUPPORTED (no tcgen05), OUT_OF_MEMORY.  Synchronous. */
+curob_status curob_surrogate_create(int max_batch, uint64_t seed, curob_surrogate* s);
+curob_status curob_surrogate_destroy(curob_surrogate s);
+
+/* AdamW hyper-parameters (lr is the default of curob_surrogate_step's
+ * callers; curob_surrogate_fit takes its own schedule). */
+curob_status curob_surrogate_set_hyper(curob_surrogate s, float lr, float beta1, float beta2,
+                                       float eps, float weight_decay);
+
+/* FP32 master parameters to / from a HOST array of CUROB_SURROGATE_PARAMS
+ * floats (synchronous).  set_params also zeroes the AdamW moments and step. */
+curob_status curob_surrogate_get_params(curob_surrogate s, float* host_params);
+curob_status curob_surrogate_set_params(curob_surrogate s, const float* host_params);
+
+/* Gradient of the loss of the last curob_surrogate_step / fit step, as a
+ * HOST array laid out like the parameters (synchronous). */
+curob_status curob_surrogate_get_grads(curob_surrogate s, float* host_grads);
+
+/* Target standardisation: set directly, read back, or computed (FP64, one
+ * kernel) as the mean and standard deviation of log(max(f - f_opt, 0) + 1)
+ * over n device values f (synchronises the stream; sd = 1 when it is 0). */
+curob_status curob_surrogate_set_standardisation(curob_surrogate s, float mu, float sd);
+curob_status curob_surrogate_get_standardisation(curob_surrogate s, float* mu, float* sd);
+curob_status curob_surrogate_standardise(curob_surrogate s, const float* f, long long n,
+                                         float f_opt, curob_stream_t stream);
+
+/* One step on a batch of B candidates x (B x 100) with exact values f (B):
+ * forward, loss, back-propagation; with update != 0 also the AdamW update at
+ * learning rate lr.  loss_out (device, may be NULL) receives the batch's
+ * mean loss.  B a multiple of 128, <= max_batch (else CAPACITY). */
+curob_status curob_surrogate_step(curob_surrogate s, const float* x, const float* f, int B,
+                                  float f_opt, float lr, int update, float* loss_out,
+                                  curob_stream_t stream);
+
+/* Trains on n samples (x: n x 100, f: n): standardises the targets (as
+ * curob_surrogate_standardise), then `epochs` passes over floor(n / batch)
+ * batches of consecutive rows, the batch order reshuffled every epoch
+ * (Fisher-Yates, seeded by shuffle_seed), learning rate on a cosine from
+ * lr_max down to lr_max / 20.  loss_hist (device, may be NULL) receives
+ * epochs * floor(n / batch) batch losses.  Uses ~512 bytes of device memory
+ * per sample for the duration of the call. */
+curob_status curob_surrogate_fit(curob_surrogate s, const float* x, const float* f, long long n,
+                                 float f_opt, int epochs, int batch, float lr_max,
+                                 uint64_t shuffle_seed, float* loss_hist, curob_stream_t stream);
+
+/* Predicted t = mu + sd * y for N candidates x (N x 100) into out (N). */
+curob_status curob_surrogate_predict(curob_surrogate s, const float* x, long long N, float* out,
+                                     curob_stream_t stream);
+
+/* Synchronises `stream` and reports (then clears) a device-side error of the
+ * surrogate's kernels (DEVICE_TIMEOUT). */
+curob_status curob_surrogate_device_status(curob_surrogate s, curob_stream_t stream);
+
+/* Indices of the k smallest of v[0..N-1] (0 <= k <= N < 2^31), equal values
+ * taken in index order, written to idx[0..k-1] in ascending index order; NaN
+ * ranks above +inf.  Radix selection on the order-preserving integer keys,
+ * exact (bit-identical to a full sort).  Uses a small stream-ordered
+ * allocation.  INVALID_ARGUMENT for k outside [0, N]. */
+curob_status curob_select_smallest(const float* v, long long N, int k, int* idx,
+                                   curob_stream_t stream);
+
+/* out[r][:] = x[idx[r]][:] for r < k (rows of D floats). */
+curob_status curob_gather_rows(const float* x, int D, const int* idx, int k, float* out,
+                               curob_stream_t stream);
+
+/* One generation of surrogate pre-screening on the current instance (D must
+ * be 100): predicts all N pool candidates (pred, N), keeps the k with the
+ * smallest prediction (idx, ascending), gathers them (x_sel, k x 100) and
+ * evaluates them exactly with curob_evaluatef (f_sel, k; k <= the
+ * instance's max_concurrency).  Errors: INVALID_DIM (D != 100), CAPACITY,
+ * INVALID_ARGUMENT, and those of curob_evaluatef. */
+curob_status curob_surrogate_screen(curob_surrogate s, int fid, const float* pool, long long N,
+                                    int k, float* pred, int* idx, float* x_sel, float* f_sel,
+                                    curob_stream_t stream);
 
 #ifdef __cplusplus
 }

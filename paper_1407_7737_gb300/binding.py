@@ -27,6 +27,8 @@ FOPT = 100.0
 # (name, restype, argtypes) of every exported entry point
 _P = ctypes.c_void_p
 _I = ctypes.c_int
+_F = ctypes.c_float
+_LL = ctypes.c_longlong
 _SIGS = [
     ("curob_initialize", _I, [_I, _I, ctypes.c_uint64]),
     ("curob_dispose", _I, []),
@@ -51,6 +53,23 @@ _SIGS = [
     ("curob_batch_status", _I, [_P, _P]),
     ("curob_batch_destroy", _I, [_P]),
     ("curob_evaluatef_multi_noalloc", _I, [_P, _P, _P, _P, _I, _P]),
+    ("curob_last_error", ctypes.c_char_p, []),
+    ("curob_surrogate_create", _I, [_I, ctypes.c_uint64, _P]),
+    ("curob_surrogate_destroy", _I, [_P]),
+    ("curob_surrogate_set_hyper", _I, [_P, _F, _F, _F, _F, _F]),
+    ("curob_surrogate_get_params", _I, [_P, _P]),
+    ("curob_surrogate_set_params", _I, [_P, _P]),
+    ("curob_surrogate_get_grads", _I, [_P, _P]),
+    ("curob_surrogate_set_standardisation", _I, [_P, _F, _F]),
+    ("curob_surrogate_get_standardisation", _I, [_P, _P, _P]),
+    ("curob_surrogate_standardise", _I, [_P, _P, _LL, _F, _P]),
+    ("curob_surrogate_step", _I, [_P, _P, _P, _I, _F, _F, _I, _P, _P]),
+    ("curob_surrogate_fit", _I, [_P, _P, _P, _LL, _F, _I, _I, _F, ctypes.c_uint64, _P, _P]),
+    ("curob_surrogate_predict", _I, [_P, _P, _LL, _P, _P]),
+    ("curob_surrogate_device_status", _I, [_P, _P]),
+    ("curob_select_smallest", _I, [_P, _LL, _I, _P, _P]),
+    ("curob_gather_rows", _I, [_P, _I, _P, _I, _P, _P]),
+    ("curob_surrogate_screen", _I, [_P, _I, _P, _LL, _I, _P, _P, _P, _P, _P]),
 ]
 EXPORTS = [s[0] for s in _SIGS]
 
@@ -89,7 +108,11 @@ def load(build_if_missing: bool = True):
 def _call(name, *args, check=True):
     rc = getattr(load(), name)(*args)
     if check and rc != 0:
-        raise CurobError(name, rc)
+        err = CurobError(name, rc)
+        detail = load().curob_last_error()
+        if rc == CODES["CUROB_ERR_CUDA"] and detail:
+            err.args = (f"{err.args[0]} ({detail.decode(errors='replace')})",)
+        raise err
     return rc
 
 
@@ -264,6 +287,110 @@ def curob_evaluatef_multi_noalloc(fids, xs, Ns, outs, stream=None, check=True):
     op = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
     return _call("curob_evaluatef_multi_noalloc", ctypes.addressof(f), ctypes.addressof(xp),
                  ctypes.addressof(nn), ctypes.addressof(op), n, _stream(stream), check=check)
+
+
+SURROGATE_INPUT = 100
+SURROGATE_HIDDEN = 256
+SURROGATE_PARAMS = 91905
+# offsets of the flat parameter vector
+SURROGATE_LAYOUT = {"W1": (0, (256, 100)), "b1": (25600, (256,)), "W2": (25856, (256, 256)),
+                    "b2": (91392, (256,)), "w3": (91648, (256,)), "b3": (91904, ())}
+
+
+def curob_last_error():
+    """Text of the last CUDA failure recorded on this thread ('' if none)."""
+    return load().curob_last_error().decode(errors="replace")
+
+
+def curob_surrogate_create(max_batch, seed, check=True):
+    """Returns the surrogate handle (an integer)."""
+    h = ctypes.c_void_p()
+    _call("curob_surrogate_create", max_batch, seed, ctypes.byref(h), check=check)
+    return h.value
+
+
+def curob_surrogate_destroy(s, check=True):
+    return _call("curob_surrogate_destroy", s, check=check)
+
+
+def curob_surrogate_set_hyper(s, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=1e-4,
+                              check=True):
+    return _call("curob_surrogate_set_hyper", s, lr, beta1, beta2, eps, weight_decay, check=check)
+
+
+def curob_surrogate_get_params(s):
+    import numpy as np
+    out = np.empty(SURROGATE_PARAMS, dtype=np.float32)
+    _call("curob_surrogate_get_params", s, out.ctypes.data)
+    return out
+
+
+def curob_surrogate_set_params(s, params, check=True):
+    import numpy as np
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.size == SURROGATE_PARAMS
+    return _call("curob_surrogate_set_params", s, p.ctypes.data, check=check)
+
+
+def curob_surrogate_get_grads(s):
+    import numpy as np
+    out = np.empty(SURROGATE_PARAMS, dtype=np.float32)
+    _call("curob_surrogate_get_grads", s, out.ctypes.data)
+    return out
+
+
+def surrogate_unflatten(v):
+    """Flat parameter (or gradient) vector -> dict of arrays (W1, b1, ...)."""
+    return {k: (v[o:o + int(__import__("numpy").prod(sh))].reshape(sh) if sh else float(v[o]))
+            for k, (o, sh) in SURROGATE_LAYOUT.items()}
+
+
+def curob_surrogate_set_standardisation(s, mu, sd, check=True):
+    return _call("curob_surrogate_set_standardisation", s, mu, sd, check=check)
+
+
+def curob_surrogate_get_standardisation(s):
+    mu, sd = ctypes.c_float(), ctypes.c_float()
+    _call("curob_surrogate_get_standardisation", s, ctypes.byref(mu), ctypes.byref(sd))
+    return mu.value, sd.value
+
+
+def curob_surrogate_standardise(s, f, n, f_opt=FOPT, stream=None, check=True):
+    return _call("curob_surrogate_standardise", s, _ptr(f), n, f_opt, _stream(stream), check=check)
+
+
+def curob_surrogate_step(s, x, f, B, f_opt=FOPT, lr=1e-3, update=1, loss_out=None, stream=None,
+                         check=True):
+    return _call("curob_surrogate_step", s, _ptr(x), _ptr(f), B, f_opt, lr, update,
+                 _ptr(loss_out), _stream(stream), check=check)
+
+
+def curob_surrogate_fit(s, x, f, n, f_opt=FOPT, epochs=4, batch=4096, lr_max=2e-3,
+                        shuffle_seed=0, loss_hist=None, stream=None, check=True):
+    return _call("curob_surrogate_fit", s, _ptr(x), _ptr(f), n, f_opt, epochs, batch, lr_max,
+                 shuffle_seed, _ptr(loss_hist), _stream(stream), check=check)
+
+
+def curob_surrogate_predict(s, x, N, out, stream=None, check=True):
+    return _call("curob_surrogate_predict", s, _ptr(x), N, _ptr(out), _stream(stream), check=check)
+
+
+def curob_surrogate_device_status(s, stream=None, check=True):
+    return _call("curob_surrogate_device_status", s, _stream(stream), check=check)
+
+
+def curob_select_smallest(v, N, k, idx, stream=None, check=True):
+    return _call("curob_select_smallest", _ptr(v), N, k, _ptr(idx), _stream(stream), check=check)
+
+
+def curob_gather_rows(x, D, idx, k, out, stream=None, check=True):
+    return _call("curob_gather_rows", _ptr(x), D, _ptr(idx), k, _ptr(out), _stream(stream),
+                 check=check)
+
+
+def curob_surrogate_screen(s, fid, pool, N, k, pred, idx, x_sel, f_sel, stream=None, check=True):
+    return _call("curob_surrogate_screen", s, fid, _ptr(pool), N, k, _ptr(pred), _ptr(idx),
+                 _ptr(x_sel), _ptr(f_sel), _stream(stream), check=check)
 
 
 # ----- tensor conveniences ---------------------------------------------------

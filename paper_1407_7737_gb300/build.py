@@ -23,7 +23,7 @@ EXTRA = {
     "curob_setup.cu": ["-fmad=false"],
 }
 SOURCES = ["curob_api.cu", "curob_instance.cu", "curob_setup.cu", "curob_simt64.cu",
-           "curob_simt32.cu", "curob_mma.cu", "curob_batch.cu"]
+           "curob_simt32.cu", "curob_mma.cu", "curob_batch.cu", "curob_mlp.cu"]
 
 
 def _deps():
@@ -57,7 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(8, len(SOURCES))) as ex:
         objs = list(ex.map(_compile, SOURCES))
     tmp = SO + f".tmp{os.getpid()}"
-    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcuda"]
+    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

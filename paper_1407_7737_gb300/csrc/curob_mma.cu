@@ -8,14 +8,18 @@
 //   TF32X3  y = yh + yl, R = Rh + Rl (TF32 halves), Z = Yh Rh + Yh Rl + Yl Rh,
 //           one FP32 accumulator;
 //   BF16X3  the same with BF16 halves;
-//   EXACT   y / sigma_m and R / tau_i (powers of two) cut into four 7-bit
-//           integer slices each, held exactly in BF16; the ten slice products
-//           of weight 2^-7(a+b), a + b <= 5, accumulate in four accumulators,
-//           one per weight.  Every partial sum is an integer below 2^24, so
-//           the FP32 accumulation is exact whatever the tensor core's
-//           rounding; z = sigma tau sum_g 2^-7g P_g to about 2^-28 of the row
-//           scale.  (The error-free splitting of matrix products of Ozaki,
-//           Ogita, Oishi and Rump, with BF16 integer slices.)
+//   EXACT   128 y / sigma_m and 128 R / tau_i (sigma, tau powers of two) cut
+//           into four integer slices each (|s| <= 128: the leading one, then
+//           8 more bits each), held exactly in BF16 and pre-scaled by their
+//           weight (s_a 2^-8(a-1)).  The leading product s1 r1 accumulates
+//           alone: every partial sum is an integer of magnitude below 2^23,
+//           so its FP32 accumulation is exact whatever the tensor core's
+//           rounding; the nine products of weight 2^-8 to 2^-24 share a
+//           second accumulator 2^-8 below it, so its rounding (and any
+//           truncation bias of the FP32 accumulation) is scaled down by
+//           2^-8; dropped products weigh <= 2^-32.  z = sigma tau 2^-14
+//           (A0 + A1), to ~2^-26 of the row scale.  (The error-free splitting of matrix products of
+//           Ozaki, Ogita, Oishi and Rump, with BF16 integer slices.)
 // The tensor core's FP32 accumulation truncates: over a 334-long block TF32X3
 // loses ~2e-6 of |z| systematically, which the functions that magnify z
 // errors (Discus, Weierstrass, Griewank-Rosenbrock, Katsuura) cannot absorb;
@@ -48,166 +52,32 @@
 #include <cstring>
 
 #include "curob_mma.hpp"
+#include "curob_tc.cuh"
 
 namespace curob {
 namespace {
 
+using namespace tc;
+
 constexpr int kTileM = 128;
 constexpr int kThreads = 320;
-constexpr int kRowBytes = 64;                    // one K-stage row: 64 B (SW64)
 constexpr int kPartBytes = kTileM * kRowBytes;   // 8 KB per A part
-constexpr unsigned long long kTimeoutNs = 2000000000ull;
 constexpr int kMaxNpad = 512;                    // TMEM columns
-constexpr int kExactNC = 128;                    // EXACT: N chunk (4 groups x 128)
+constexpr int kExactMaxNC = 192;                 // EXACT: widest N chunk
+constexpr int kExactAcc1 = 256;                  // EXACT: TMEM column of accumulator 1
 constexpr int kSigRing = 8;                      // EXACT: row scales in flight
 
 enum Mode : int { M_TF32 = 0, M_BF16 = 1, M_EXACT = 2 };
 
-// -------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
+// EXACT splits a block's npad output columns into nchunk equal chunks of at
+// most kExactMaxNC (a multiple of 16 wide): accumulators 0 and 1 of a chunk
+// sit at TMEM columns [0, nw) and [256, 256 + nw).
+__host__ __device__ inline int exact_nchunk(int npad) {
+  return (npad + kExactMaxNC - 1) / kExactMaxNC;
 }
-__device__ __forceinline__ unsigned long long globaltimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait on the phase of `parity`; false when the CTA aborts or the
-// wait exceeds kTimeoutNs (then the status word gets DEV_TIMEOUT).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          int* status) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = globaltimer();
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort_flag) return false;
-    if (globaltimer() - t0 > kTimeoutNs) {
-      *abort_flag = 1;
-      atomicExch(status, DEV_TIMEOUT);
-      return false;
-    }
-  }
-  return true;
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-// Barrier of the 4 producer warps on an mbarrier (count 4), bounded like
-// every other wait; `phase` counts its uses.
-__device__ __forceinline__ bool producers_sync(uint64_t* bar, uint32_t& phase,
-                                               volatile int* abort_flag, int* status) {
-  __syncwarp();
-  if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
-  const bool ok = mbar_wait(bar, phase & 1u, abort_flag, status);
-  ++phase;
-  return ok;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tc_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-template <bool kTf32>
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                       uint32_t accumulate) {
-  if constexpr (kTf32) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-  }
-}
-// 32 lanes x 32 consecutive FP32 columns: thread i of the warp gets row
-// (its TMEM lane) columns [col, col+32).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Shared-memory matrix descriptor: K-major, 64-byte swizzle, rows of 64 B,
-// 8-row groups 512 B apart (SBO), descriptor version 1.
-__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1u << 16;                       // LBO (unused for swizzled K-major)
-  d |= (uint64_t)((512u >> 4) & 0x3FFFu) << 32;  // SBO
-  d |= (uint64_t)1u << 46;                       // version
-  d |= (uint64_t)4u << 61;                       // SWIZZLE_64B
-  return d;
-}
-// Instruction descriptor: FP32 accumulator, A/B format (TF32 = 2, BF16 = 1),
-// both K-major, N >> 3, M >> 4.
-__host__ __device__ constexpr uint32_t idesc_make(uint32_t fmt, uint32_t M, uint32_t N) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
-}
-
-// Byte offset of (row, byte-in-row) in the 64-byte-swizzled image: the
-// 16-byte chunk index (bits 4-5) XOR bits 7-8 of the linear offset.
-__host__ __device__ __forceinline__ uint32_t swz64(uint32_t row, uint32_t byte_in_row) {
-  uint32_t off = row * kRowBytes + byte_in_row;
-  return off ^ (((off >> 7) & 3u) << 4);
-}
-
-__device__ __forceinline__ uint32_t to_tf32(float v) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-  return r;
-}
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-  return *reinterpret_cast<uint32_t*>(&h);
+__host__ __device__ inline int exact_nw(int npad) {
+  const int n = exact_nchunk(npad);
+  return ((npad + n - 1) / n + 15) / 16 * 16;
 }
 
 // x - o with o = ohi + olo as a double-float (yh, yl): TwoSum(x, -ohi) is
@@ -271,20 +141,52 @@ struct EpiSeg {
 };
 
 // Kinds whose per-variable term calls transcendentals with slow paths (large
-// arguments): their term is one out-of-line call, so the unrolled chunk loop
-// stays small; contributions come back by value (no local memory).
+// arguments): their terms are out-of-line calls on four variables at a time,
+// so the unrolled chunk loop stays small while the four independent
+// evaluations interleave (one epilogue warp per scheduler has no other warp
+// to hide their latency); contributions come back by value (no local memory).
 __host__ __device__ constexpr bool kind_is_heavy(int k) {
   return k == K_POWERS || k == K_WEIERSTRASS || k == K_GRIEWANK || k == K_SCHAFFER7 ||
          k == K_EGR || k == K_SCHWEFEL || k == K_KATSUURA || k == K_SCHAFFER6;
 }
-__device__ __noinline__ float4 heavy_term(int kind, float z, float u, int gi, float gn, float aux,
-                                          float kat_e) {
-  Acc<float> a = acc_zero<float>();
-  elem_term_f32(kind, z, u, gi, gn, aux, kat_e, a);
-  return make_float4(a.a0, a.a1, a.a2, a.p);
+// Sums (a0, a1, a2) and product (p) of the terms of the first n <= 4 of four
+// consecutive variables.
+template <int KIND>
+__device__ __noinline__ float4 heavy_term4(float4 z, float4 u, int gi, float gn, float4 aux,
+                                           float kat_e, int n) {
+  const float zs[4] = {z.x, z.y, z.z, z.w}, us[4] = {u.x, u.y, u.z, u.w};
+  const float as[4] = {aux.x, aux.y, aux.z, aux.w};
+  Acc<float> t[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    t[e] = acc_zero<float>();
+    elem_term_f32(KIND, zs[e], us[e], gi + e, gn, as[e], kat_e, t[e]);
+  }
+  float4 r = make_float4(0.f, 0.f, 0.f, 1.f);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    if (e < n) {
+      r.x += t[e].a0;
+      r.y += t[e].a1;
+      r.z += t[e].a2;
+      r.w *= t[e].p;
+    }
+  }
+  return r;
 }
-__device__ __noinline__ float heavy_pair(int kind, float zp, float z) {
-  return pair_term<float>(kind, zp, z);
+// Sum of the pair terms (zp_e, z_e) of four consecutive variables, e in
+// [first, n).
+template <int KIND>
+__device__ __noinline__ float heavy_pair4(float4 zp, float4 z, int first, int n) {
+  const float ps[4] = {zp.x, zp.y, zp.z, zp.w}, zs[4] = {z.x, z.y, z.z, z.w};
+  float t[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) t[e] = pair_term<float>(KIND, ps[e], zs[e]);
+  float r = 0.f;
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+    if (e >= first && e < n) r += t[e];
+  return r;
 }
 
 // 32 accumulator columns [c, c + cend) of one row, for a fixed kind: the
@@ -296,37 +198,59 @@ __device__ __forceinline__ void epi_chunk_k(const float* v, int c, int cend, con
                            KIND == K_SCHAFFER6);
   constexpr bool kAux = (KIND == K_ELLIPTIC || KIND == K_POWERS || KIND == K_GRIEWANK);
   Acc<float> part = acc_zero<float>();
-  float zprev = st.zprev;
+  if constexpr (kind_is_heavy(KIND)) {
+    const bool opens = (c == 0 && es.gfirst);  // column 0 opens the function
+    float zlast = st.zprev;
 #pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    if (k < cend) {
-      const int col = c + k;
-      const float u = v[k] * es.s;  // z before its offset
-      const float z = u + es.c0;
-      if constexpr (kind_is_heavy(KIND)) {
-        if (KIND != K_SCHAFFER7 && KIND != K_EGR && KIND != K_SCHAFFER6) {
-          const float4 t = heavy_term(KIND, z, u, es.gpos + col, es.gnT,
-                                      kAux ? es.aux[col] : 0.f, es.kat_e);
+    for (int g = 0; g < 32; g += 4) {
+      if (g < cend) {
+        const int n = min(4, cend - g);
+        float4 u4 = make_float4(v[g] * es.s, v[g + 1] * es.s, v[g + 2] * es.s, v[g + 3] * es.s);
+        float4 z4 = make_float4(u4.x + es.c0, u4.y + es.c0, u4.z + es.c0, u4.w + es.c0);
+        if constexpr (kPairs) {
+          const float zp0 = g == 0 ? st.zprev : v[g - 1] * es.s + es.c0;
+          const float4 zp4 = make_float4(zp0, z4.x, z4.y, z4.z);
+          part.a0 += heavy_pair4<KIND>(zp4, z4, (g == 0 && opens) ? 1 : 0, n);
+        } else {
+          float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
+          if constexpr (kAux) {
+            const float* ap = es.aux + c + g;
+            a4 = make_float4(ap[0], n > 1 ? ap[1] : 0.f, n > 2 ? ap[2] : 0.f, n > 3 ? ap[3] : 0.f);
+          }
+          const float4 t = heavy_term4<KIND>(z4, u4, es.gpos + c + g, es.gnT, a4, es.kat_e, n);
           part.a0 += t.x;
           part.a1 += t.y;
           part.a2 += t.z;
           part.p *= t.w;
         }
-      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (e == n - 1) zlast = v[g + e] * es.s + es.c0;
+      }
+    }
+    if (opens) st.zfirst = v[0] * es.s + es.c0;
+    st.zprev = zlast;
+  } else {
+    float zprev = st.zprev;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      if (k < cend) {
+        const int col = c + k;
+        const float u = v[k] * es.s;  // z before its offset
+        const float z = u + es.c0;
         elem_term_f32(KIND, z, u, es.gpos + col, es.gnT, kAux ? es.aux[col] : 0.f, es.kat_e,
                       part);
+        if (kPairs) {
+          if (col == 0 && es.gfirst) st.zfirst = z;
+          else part.a0 += pair_term<float>(KIND, zprev, z);
+        } else if (col == 0 && es.gfirst) {
+          st.zfirst = z;
+        }
+        zprev = z;
       }
-      if (kPairs) {
-        if (col == 0 && es.gfirst) st.zfirst = z;
-        else if (kind_is_heavy(KIND)) part.a0 += heavy_pair(KIND, zprev, z);
-        else part.a0 += pair_term<float>(KIND, zprev, z);
-      } else if (col == 0 && es.gfirst) {
-        st.zfirst = z;
-      }
-      zprev = z;
     }
+    st.zprev = zprev;
   }
-  st.zprev = zprev;
   st.a0 += (double)part.a0;
   st.a1 += (double)part.a1;
   st.a2 += (double)part.a2;
@@ -545,7 +469,7 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
         }
         if (!producers_sync(prod_bar, pphase, abort_flag, tb.status)) { ok = false; break; }
         const int nslab = sg.npad / kKs;
-        const int nchunk = kMode == M_EXACT ? (sg.npad + kExactNC - 1) / kExactNC : 1;
+        const int nchunk = kMode == M_EXACT ? exact_nchunk(sg.npad) : 1;
         const int total = nslab * nchunk;  // stages of this block
         const uint32_t it0 = it;
         // raw x of stage q, row rr: kKs floats at part 0 row rr (first 16)
@@ -643,7 +567,8 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
               *reinterpret_cast<uint4*>(A + kPartBytes + off) =
                   make_uint4(lw[0], lw[1], lw[2], lw[3]);
             } else {
-              // four 7-bit integer slices of y / sigma (exact in BF16)
+              // four integer slices of 128 y / sigma (exact in BF16),
+              // pre-scaled by their weight
               uint32_t w[4][4];
 #pragma unroll
               for (int qq = 0; qq < 4; ++qq) {
@@ -653,15 +578,15 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
                   const int k = c * 8 + 2 * qq + e;
                   const float v = yh[k] * isig * 128.f;
                   const float y1 = rintf(v);
-                  const float v2 = ((v - y1) + yl[k] * isig * 128.f) * 128.f;
+                  const float v2 = ((v - y1) + yl[k] * isig * 128.f) * 256.f;
                   const float y2 = rintf(v2);
-                  const float v3 = (v2 - y2) * 128.f;
+                  const float v3 = (v2 - y2) * 256.f;
                   const float y3 = rintf(v3);
-                  const float y4 = rintf((v3 - y3) * 128.f);
+                  const float y4 = rintf((v3 - y3) * 256.f);
                   sl[e][0] = y1;
-                  sl[e][1] = y2;
-                  sl[e][2] = y3;
-                  sl[e][3] = y4;
+                  sl[e][1] = y2 * 0.00390625f;
+                  sl[e][2] = y3 * 1.52587890625e-05f;
+                  sl[e][3] = y4 * 5.9604644775390625e-08f;
                 }
 #pragma unroll
                 for (int pp = 0; pp < 4; ++pp) w[pp][qq] = pack_bf16(sl[0][pp], sl[1][pp]);
@@ -716,32 +641,27 @@ __device__ void epilogue_tile(const MmaArgs& a, const Smem& m, long long row0, R
         es.gfirst = sg.gfirst;
         const float* tau = a.tau + sg.tau_off;
         if (sg.gfirst) st.open();
-        const int nchunk = kMode == M_EXACT ? (sg.npad + kExactNC - 1) / kExactNC : 1;
+        const int nchunk = kMode == M_EXACT ? exact_nchunk(sg.npad) : 1;
+        const int nw = kMode == M_EXACT ? exact_nw(sg.npad) : sg.npad;
         for (int cc = 0; cc < nchunk; ++cc, ++chunk_it) {
           if (!mbar_wait(tmem_full, chunk_it & 1u, abort_flag, tb.status)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const int c_lo = kMode == M_EXACT ? cc * kExactNC : 0;
-          const int c_hi = kMode == M_EXACT ? min(sg.n, c_lo + kExactNC) : sg.n;
+          const int c_lo = kMode == M_EXACT ? cc * nw : 0;
+          const int c_hi = kMode == M_EXACT ? min(sg.n, c_lo + nw) : sg.n;
           for (int c = c_lo; c < c_hi; c += 32) {
             float v[32];
             if constexpr (kMode == M_EXACT) {
-              float g1[32], g2[32], g3[32];
+              float g1[32];
               const uint32_t lc = (uint32_t)(c - c_lo);
               tmem_ld32(t_lane + lc, v);
-              tmem_ld32(t_lane + kExactNC + lc, g1);
-              tmem_ld32(t_lane + 2 * kExactNC + lc, g2);
-              tmem_ld32(t_lane + 3 * kExactNC + lc, g3);
+              tmem_ld32(t_lane + kExactAcc1 + lc, g1);
               const float base = sig * 6.103515625e-05f;  // sigma 2^-14
 #pragma unroll
-              for (int k = 0; k < 32; ++k) {
-                float t = fmaf(g3[k], 0.0078125f, g2[k]);
-                t = fmaf(t, 0.0078125f, g1[k]);
-                t = fmaf(t, 0.0078125f, v[k]);
-                v[k] = (c + k < c_hi) ? t * (base * tau[c + k]) : 0.f;
-              }
+              for (int k = 0; k < 32; ++k)
+                v[k] = (c + k < c_hi) ? (v[k] + g1[k]) * (base * tau[c + k]) : 0.f;
             } else {
               tmem_ld32(t_lane + (uint32_t)c, v);
             }
@@ -772,9 +692,10 @@ __device__ void mma_tile(const MmaArgs& a, const Smem& m, long long row0, RoleSt
         for (int si = 0; si < Cm.nseg && ok; ++si) {
           const Segment sg = tb.seg[Cm.seg0 + si];
           const int nslab = sg.npad / kKs;
-          const int nchunk = kMode == M_EXACT ? (sg.npad + kExactNC - 1) / kExactNC : 1;
+          const int nchunk = kMode == M_EXACT ? exact_nchunk(sg.npad) : 1;
+          const int nw = kMode == M_EXACT ? exact_nw(sg.npad) : sg.npad;
           for (int cc = 0; cc < nchunk && ok; ++cc, ++chunk_it) {
-            const int nc = kMode == M_EXACT ? min(kExactNC, sg.npad - cc * kExactNC) : sg.npad;
+            const int nc = kMode == M_EXACT ? min(nw, sg.npad - cc * nw) : sg.npad;
             const int n0 = nc > 256 ? 256 : nc;  // N per MMA <= 256
             const int n1 = nc - n0;
             const uint32_t id0 = idesc_make(C::kFmt, kTileM, (uint32_t)n0);
@@ -800,16 +721,16 @@ __device__ void mma_tile(const MmaArgs& a, const Smem& m, long long row0, RoleSt
                 const uint32_t ko = (uint32_t)(kk * C::kMmaK * kEl);  // 32 B per K step
                 const uint32_t first = (t == 0 && kk == 0) ? 0u : 1u;
                 if constexpr (kMode == M_EXACT) {
-                  // slice pairs (a, b) of weight a + b = w <= 3 into accumulator w
+                  // s1 r1 into accumulator 0; the pre-scaled products of
+                  // weight 2^-8 to 2^-24 (a + b <= 3) into accumulator 1
+                  constexpr int kPa[10] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
+                  constexpr int kPb[10] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
 #pragma unroll
-                  for (int w = 0; w < 4; ++w) {
-                    const uint32_t dt = tmem_base + (uint32_t)(w * kExactNC);
-#pragma unroll
-                    for (int ia = 0; ia <= w; ++ia) {
-                      const uint64_t da = sdesc_sw64(sa + ia * kPartBytes + ko);
-                      const uint64_t db = sdesc_sw64(sb + (w - ia) * bpart + ko);
-                      tc_mma<false>(dt, da, db, id0, (ia == 0) ? first : 1u);
-                    }
+                  for (int pq = 0; pq < 10; ++pq) {
+                    const uint32_t dt = tmem_base + (pq == 0 ? 0u : (uint32_t)kExactAcc1);
+                    const uint64_t da = sdesc_sw64(sa + kPa[pq] * kPartBytes + ko);
+                    const uint64_t db = sdesc_sw64(sb + kPb[pq] * bpart + ko);
+                    tc_mma<false>(dt, da, db, id0, (pq <= 1) ? first : 1u);
                   }
                 } else {
                   const uint64_t dah = sdesc_sw64(sa + ko), dal = sdesc_sw64(sa + kPartBytes + ko);
@@ -847,13 +768,14 @@ __device__ void loader_tile(const MmaArgs& a, const Smem& m, long long row0, Rol
         for (int si = 0; si < Cm.nseg && ok; ++si) {
           const Segment sg = tb.seg[Cm.seg0 + si];
           const int nslab = sg.npad / kKs;
-          const int nchunk = kMode == M_EXACT ? (sg.npad + kExactNC - 1) / kExactNC : 1;
+          const int nchunk = kMode == M_EXACT ? exact_nchunk(sg.npad) : 1;
+          const int nw = kMode == M_EXACT ? exact_nw(sg.npad) : sg.npad;
           const long long fl = image_floats(sg.npad);
           const uint8_t* base = a.img + ((size_t)sg.img_off + (size_t)kMode * fl) * 4;
           for (int cc = 0; cc < nchunk && ok; ++cc) {
-            const int nc = kMode == M_EXACT ? min(kExactNC, sg.npad - cc * kExactNC) : sg.npad;
+            const int nc = kMode == M_EXACT ? min(nw, sg.npad - cc * nw) : sg.npad;
             const uint32_t bytes = (uint32_t)(kParts * nc * kRowBytes);
-            const uint8_t* src = base + (size_t)cc * nslab * kParts * kExactNC * kRowBytes;
+            const uint8_t* src = base + (size_t)cc * nslab * kParts * nw * kRowBytes;
             for (int t = 0; t < nslab; ++t, ++it) {
               const int stage = it % a.nstage;
               const uint32_t ph = (it / a.nstage) & 1u;
@@ -980,19 +902,22 @@ __global__ void build_image_kernel(const ImgJob* jobs, const double* R, uint8_t*
       *reinterpret_cast<__nv_bfloat16*>(hi + off) = h;
       *reinterpret_cast<__nv_bfloat16*>(lo + off) = l;
     }
-    {  // EXACT: chunk cc = row / 128, stage t = col / 32
-      const int cc = row / kExactNC, rr = row % kExactNC;
-      const int nc = min(kExactNC, npad - cc * kExactNC);
+    {  // EXACT: chunk cc = row / nw, stage t = col / 32, four pre-scaled slices
+      const int nw = exact_nw(npad);
+      const int cc = row / nw, rr = row % nw;
+      const int nc = min(nw, npad - cc * nw);
       const int t = col / 32, k = col % 32;
       uint8_t* st = base + (size_t)2 * fl * 4 +
-                    ((size_t)cc * nslab32 * 4 * kExactNC + (size_t)t * 4 * nc) * kRowBytes;
+                    ((size_t)cc * nslab32 * 4 * nw + (size_t)t * 4 * nc) * kRowBytes;
       const uint32_t off = swz64((uint32_t)rr, (uint32_t)(k * 2));
       double w = v / (double)tau[J.tau_off + row] * 128.0;  // exact: tau is 2^f
+      double scale = 1.0;
       for (int s = 0; s < 4; ++s) {
         const double yv = rint(w);
         *reinterpret_cast<__nv_bfloat16*>(st + (size_t)s * nc * kRowBytes + off) =
-            __double2bfloat16(yv);
-        w = (w - yv) * 128.0;
+            __double2bfloat16(yv * scale);
+        w = (w - yv) * 256.0;
+        scale *= 0.00390625;
       }
     }
   }
@@ -1025,7 +950,7 @@ template <int kMode>
 cudaError_t launch_mode(const MmaPlan& p, const Tables& tb, const Function& F, const float* x,
                         int N, float* out, cudaStream_t st) {
   const int npad_max = npad_of(F.max_n);
-  const int ncmax = kMode == M_EXACT ? std::min(npad_max, kExactNC) : npad_max;
+  const int ncmax = kMode == M_EXACT ? std::min(npad_max, kExactMaxNC) : npad_max;
   const size_t sb = stage_bytes_for<kMode>(ncmax);
   const size_t ctrl = ctrl_bytes();
   const int nstage = (int)std::min<size_t>(4, (219 * 1024 - ctrl) / sb);
@@ -1167,7 +1092,7 @@ struct BatchGeom {
 };
 BatchGeom batch_geom() {
   BatchGeom g;
-  const size_t sb = stage_bytes_for<M_EXACT>(kExactNC);
+  const size_t sb = stage_bytes_for<M_EXACT>(kExactMaxNC);
   g.stage_bytes = (int)sb;
   g.nstage = (int)std::min<size_t>(4, (219 * 1024 - ctrl_bytes()) / sb);
   g.smem = g.nstage * sb + ctrl_bytes() + 1024;

@@ -46,3 +46,13 @@ def ragged_instances(n_inst: int, seed: int, dims=(10, 30, 50, 100, 500, 1000),
     Ds = rng.choice(np.asarray(dims), size=n_inst)
     Ns = np.round(np.exp(rng.uniform(np.log(nmin), np.log(nmax), size=n_inst)))
     return [(int(f), int(d), int(n)) for f, d, n in zip(fids, Ds, Ns)]
+
+
+def shuffled_mixture(N: int, D: int, seed: int, center, frac_near: float = 0.3,
+                     sigma: float = 10.0) -> np.ndarray:
+    """Training and screening pools of the learned pre-screen: ``frac_near``
+    of the rows Gaussian around ``center`` (width ``sigma``), the rest uniform
+    in the box, rows in random order."""
+    x = mixed(N, D, seed, center, frac_near, sigma)
+    rng = np.random.default_rng([seed, 0x5A1F, D, N])
+    return x[rng.permutation(N)]
