@@ -253,11 +253,15 @@ __device__ inline T weierstrass_const() {
 // Katsuura inner sum (Sec. 4.11): sum_{j=1}^{32} |2^j z - [2^j z]| / 2^j.
 template <typename T>
 __device__ inline T katsuura_inner(T z) {
-  T s = T(0), tj = T(1);
+  // 2^j z and the division by 2^j are exact scalings: the reciprocal power
+  // of two gives the same value as the division.
+  T s = T(0), tj = T(1), itj = T(1);
+#pragma unroll 8
   for (int j = 1; j <= 32; ++j) {
     tj = tj * T(2);
+    itj = itj * T(0.5);
     T v = tj * z;
-    s += m_fabs(v - m_rint(v)) / tj;
+    s += m_fabs(v - m_rint(v)) * itj;
   }
   return s;
 }
@@ -330,10 +334,22 @@ __device__ inline float schwefel_term_f32(float z, float gn) {
     const float sc = 20.51752290671326630f;      // sqrt(c)
     const float ssc = 0.99528264515390726719f;   // sin(sqrt(c))
     const float sum = sqrtf(w) + sc;
-    const float dg = 2.f * w * cosf(0.5f * sum) * sinf(z / (2.f * sum)) + z * ssc;
+    const float dg = 2.f * w * cosf(0.5f * sum) * sinf(0.5f * z * __frcp_rn(sum)) + z * ssc;
     return 1.2727566295939802e-5f - dg;
   }
-  return 418.9829f - schwefel_g1(z + 420.9687462275036f, gn);
+  // |w| > 500 (or w <= 0): g1 of Eq. basic_schwefel with the remainder
+  // m = |w| mod 500 taken exactly (|w| - 500 q is representable, q corrected
+  // by one step) instead of by fmodf, and the penalty scaled by a reciprocal.
+  const float wv = z + 420.9687462275036f;
+  const float a = fabsf(wv);
+  if (a <= 500.f) return 418.9829f - wv * sinf(sqrtf(a));
+  const float q = floorf(a * 0.002f);
+  float m = fmaf(-500.f, q, a);
+  if (m < 0.f) m += 500.f;
+  else if (m >= 500.f) m -= 500.f;
+  const float t = a - 500.f;
+  const float g = (500.f - m) * sinf(sqrtf(500.f - m));
+  return 418.9829f - ((wv > 0.f ? g : -g) - t * t * __frcp_rn(10000.f * gn));
 }
 
 __device__ inline void elem_term_f32(int kind, float z, float u, int gi, float gn, float aux,

@@ -208,7 +208,7 @@ __device__ __forceinline__ void epi_chunk_k(const float* v, int c, int cend, con
         float4 u4 = make_float4(v[g] * es.s, v[g + 1] * es.s, v[g + 2] * es.s, v[g + 3] * es.s);
         float4 z4 = make_float4(u4.x + es.c0, u4.y + es.c0, u4.z + es.c0, u4.w + es.c0);
         if constexpr (kPairs) {
-          const float zp0 = g == 0 ? st.zprev : v[g - 1] * es.s + es.c0;
+          const float zp0 = g == 0 ? st.zprev : v[g > 0 ? g - 1 : 0] * es.s + es.c0;
           const float4 zp4 = make_float4(zp0, z4.x, z4.y, z4.z);
           part.a0 += heavy_pair4<KIND>(zp4, z4, (g == 0 && opens) ? 1 : 0, n);
         } else {
@@ -476,26 +476,30 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
         // and part 1 row rr (next 16).  Lanes walk a row's (sorted) columns,
         // so one instruction touches one or two rows' few sectors; each
         // thread's copies arrive on gbar[stage] when they land.
-        auto issue = [&](int q) -> bool {
+        const float* xbase = a.x;
+        const long long nrows = a.N;
+        const int nst = a.nstage, sbytes = a.stage_bytes, nvalid = sg.n;
+        auto issue = [=](int q) -> bool {
           const uint32_t g = it0 + (uint32_t)q;
-          const int stage = g % a.nstage;
-          if (!mbar_wait(&empty[stage], ((g / a.nstage) & 1u) ^ 1u, abort_flag, tb.status))
+          const int stage = g % nst;
+          if (!mbar_wait(&empty[stage], ((g / nst) & 1u) ^ 1u, abort_flag, tb.status))
             return false;
-          uint8_t* A = stages + (size_t)stage * a.stage_bytes;
+          uint8_t* A = stages + (size_t)stage * sbytes;
           const int t = q % nslab;
           constexpr int kRowsPerInst = 32 / kKs;            // 2 (TF32) or 1
           const int k = lane % kKs;                         // column of the stage
           const int j = t * kKs + k;
-          const bool cin = j < sg.n;
+          const bool cin = j < nvalid;
           const int col = cin ? tabS[j] : 0;
           const uint32_t dcol = (uint32_t)((k >> 4) * kPartBytes + (k & 15) * 4);
+          const uint32_t dbase = smem_u32(A) + dcol;
 #pragma unroll 4
           for (int i = 0; i < 32 / kRowsPerInst; ++i) {
             const int rr = warp * 32 + i * kRowsPerInst + lane / kKs;
             const long long gr = row0 + rr;
-            const bool in = cin && gr < a.N;
-            const float* src = in ? a.x + gr * (long long)D + col : a.x;
-            const uint32_t dst = smem_u32(A + rr * kRowBytes) + dcol;
+            const bool in = cin && gr < nrows;
+            const float* src = in ? xbase + gr * (long long)D + col : xbase;
+            const uint32_t dst = dbase + (uint32_t)(rr * kRowBytes);
             asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src),
                          "r"(in ? 4 : 0)
                          : "memory");
@@ -515,40 +519,40 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
           const int stage = it % a.nstage;
           uint8_t* A = stages + (size_t)stage * a.stage_bytes;
           const int t = q % nslab;
-          float yh[kKs], yl[kKs];
+          // the row's raw x of this stage, read before any part is overwritten
+          float4 xr[kKs / 4];
 #pragma unroll
-          for (int k = 0; k < kKs; k += 4) {
-            const float4 xv = *reinterpret_cast<const float4*>(
-                A + (k >> 4) * kPartBytes + r * kRowBytes + (k & 15) * 4);
-            const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int j = t * kKs + k + u;
-              if (vrow && j < sg.n) {
-                shift_ff(xs[u], tabH[j], tabL[j], yh[k + u], yl[k + u]);
-              } else {
-                yh[k + u] = 0.f;
-                yl[k + u] = 0.f;
-              }
-            }
-          }
-          if (q < nslab) {  // first chunk: ||x - o||^2 of the row
-            float d2p = 0.f;
-#pragma unroll
-            for (int k = 0; k < kKs; ++k) d2p = fmaf(yh[k], yh[k], d2p);
-            d2 += (double)d2p;
-          }
+          for (int k = 0; k < kKs; k += 4)
+            xr[k / 4] = *reinterpret_cast<const float4*>(A + (k >> 4) * kPartBytes +
+                                                         r * kRowBytes + (k & 15) * 4);
+          constexpr int kPer = 16 / kEl;  // elements per 16-byte chunk
+          float d2p = 0.f;
           // one 64-byte row per part = four 16-byte chunks, each stored whole
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
+            float yh[kPer], yl[kPer];
+#pragma unroll
+            for (int e = 0; e < kPer; ++e) {
+              const int k = c * kPer + e;
+              const int j = t * kKs + k;
+              const float4 q4 = xr[k / 4];
+              const float xv = (k & 3) == 0 ? q4.x : (k & 3) == 1 ? q4.y : (k & 3) == 2 ? q4.z : q4.w;
+              if (vrow && j < sg.n) {
+                shift_ff(xv, tabH[j], tabL[j], yh[e], yl[e]);
+              } else {
+                yh[e] = 0.f;
+                yl[e] = 0.f;
+              }
+              d2p = fmaf(yh[e], yh[e], d2p);
+            }
             const uint32_t off = swz64((uint32_t)r, (uint32_t)(c * 16));
             if constexpr (kMode == M_TF32) {
               uint32_t hw[4], lw[4];
 #pragma unroll
               for (int qq = 0; qq < 4; ++qq) {
-                const float a = yh[c * 4 + qq];
+                const float a = yh[qq];
                 hw[qq] = to_tf32(a);
-                lw[qq] = to_tf32((a - __uint_as_float(hw[qq])) + yl[c * 4 + qq]);
+                lw[qq] = to_tf32((a - __uint_as_float(hw[qq])) + yl[qq]);
               }
               *reinterpret_cast<uint4*>(A + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
               *reinterpret_cast<uint4*>(A + kPartBytes + off) =
@@ -557,11 +561,10 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
               uint32_t hw[4], lw[4];
 #pragma unroll
               for (int qq = 0; qq < 4; ++qq) {
-                const float a = yh[c * 8 + 2 * qq], b = yh[c * 8 + 2 * qq + 1];
+                const float a = yh[2 * qq], b = yh[2 * qq + 1];
                 hw[qq] = pack_bf16(a, b);
                 const float2 hf = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&hw[qq]));
-                lw[qq] = pack_bf16((a - hf.x) + yl[c * 8 + 2 * qq],
-                                   (b - hf.y) + yl[c * 8 + 2 * qq + 1]);
+                lw[qq] = pack_bf16((a - hf.x) + yl[2 * qq], (b - hf.y) + yl[2 * qq + 1]);
               }
               *reinterpret_cast<uint4*>(A + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
               *reinterpret_cast<uint4*>(A + kPartBytes + off) =
@@ -575,7 +578,7 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
                 float sl[2][4];
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
-                  const int k = c * 8 + 2 * qq + e;
+                  const int k = 2 * qq + e;
                   const float v = yh[k] * isig * 128.f;
                   const float y1 = rintf(v);
                   const float v2 = ((v - y1) + yl[k] * isig * 128.f) * 256.f;
@@ -597,6 +600,7 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
                     make_uint4(w[pp][0], w[pp][1], w[pp][2], w[pp][3]);
             }
           }
+          if (q < nslab) d2 += (double)d2p;  // first chunk: ||x - o||^2 of the row
           fence_proxy_async();
           __syncwarp();
           if (lane == 0) mbar_arrive(&full[stage]);
