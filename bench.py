@@ -62,16 +62,22 @@ def parse():
 # --------------------------------------------------------------------------
 # distributed plumbing (barrier + max over ranks only)
 # --------------------------------------------------------------------------
-def dist_setup(args):
+def dist_setup(args, backend=None):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     pg = None
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl" if args.impl == "curob" else "gloo")
+        dist.init_process_group(backend or ("nccl" if args.impl == "curob" else "gloo"))
         pg = dist
     return rank, world, local, pg
+
+
+def weak_throughput(evals_per_rank, world, ms_step_max):
+    """Whole-job evaluations/s: every rank evaluates its own batches (no
+    exchange), the step time is the slowest rank's."""
+    return evals_per_rank * world / (ms_step_max / 1e3)
 
 
 def dist_max(pg, v, device):
@@ -230,8 +236,7 @@ def run_curob(args):
             launch_ms[fid] += evs[s][fid][0].elapsed_time(evs[s][fid][1])
     launch_ms /= args.steps
     ms_step = dist_max(pg, ms_total / args.steps, dev)
-    evals = NFUN * N * world
-    value = evals / (ms_step / 1e3)
+    value = weak_throughput(NFUN * N, world, ms_step)
 
     modes = [cu.curob_query_precision(f) for f in range(NFUN)]
 

@@ -51,11 +51,11 @@ typedef enum {
 /* Rotation-contraction precision of curob_evaluatef (the paper evaluates FP32
  * plainly; these are this library's choices).  TF32X3: three TF32
  * tensor-core products per term (hi*hi + hi*lo + lo*hi), FP32 accumulation.
- * BF16X3: the same with BF16 halves.  EXACT: both operands cut into three
+ * BF16X3: the same with BF16 halves.  EXACT: both operands cut into four
  * integer slices held exactly in BF16; the leading slice product is
- * accumulated exactly (every partial sum an integer below 2^23), the five
+ * accumulated exactly (every partial sum an integer below 2^23), the nine
  * lower-weight products in a second FP32 accumulator 2^-8 below it; z to
- * about 2^-24 of each candidate's |x - o|_max, with no accumulation bias.
+ * about 2^-26 of each candidate's |x - o|_max.
  * SIMT: FP32 CUDA cores with a compensated dot product.  AUTO (default):
  * EXACT for functions containing Discus, Weierstrass, expanded
  * Griewank-Rosenbrock or Katsuura (they magnify z errors), TF32X3 for the

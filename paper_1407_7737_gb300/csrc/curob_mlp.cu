@@ -37,6 +37,7 @@
 #include "../../include/curob.h"
 #include "curob_mlp.cuh"
 #include "curob_tc.cuh"
+#include "curob_tmap.hpp"
 
 namespace curob {
 bool device_accessible(const void* p);
@@ -681,42 +682,12 @@ curob_status fail(const char* where, cudaError_t e = cudaSuccess) {
            e != cudaSuccess ? cudaGetErrorString(e) : "");
   return CUROB_ERR_CUDA;
 }
-// cuTensorMapEncodeTiled, looked up through the runtime so that the library
-// does not link the driver library directly (it loads without a GPU).
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-    else
-      cudaGetLastError();
-  });
-  return fn;
-}
-
 // 2-D BF16 tensor map, 32-element (64-byte) inner box, 64-byte swizzle,
 // zero fill outside the tensor.
 bool make_map(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t rows, uint64_t row_bytes,
               uint32_t box_rows) {
-  EncodeTiledFn enc = encode_fn();
-  if (!enc) return false;
-  cuuint64_t gdim[2] = {inner, rows};
-  cuuint64_t gstr[1] = {row_bytes};
-  cuuint32_t box[2] = {32, box_rows};
-  cuuint32_t es[2] = {1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), gdim, gstr, box, es,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return encode_2d(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, ptr, inner, rows, row_bytes, 32, box_rows,
+                   CU_TENSOR_MAP_SWIZZLE_64B);
 }
 
 template <int kEpi>

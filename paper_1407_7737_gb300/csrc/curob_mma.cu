@@ -60,10 +60,13 @@ namespace {
 using namespace tc;
 
 constexpr int kTileM = 128;
-constexpr int kThreads = 320;
-constexpr int kPartBytes = kTileM * kRowBytes;   // 8 KB per A part
+constexpr int kThreads = 448;  // 8 producer, 4 epilogue, MMA and loader warps
+constexpr int kMmaWarp = 12, kLoaderWarp = 13;
 constexpr int kMaxNpad = 512;                    // TMEM columns
 constexpr int kExactMaxNC = 192;                 // EXACT: widest N chunk
+constexpr int kMaxStages = 6;                    // K stages in flight
+constexpr int kCtrlHeader = 512;                 // barrier header of the control block
+constexpr size_t kSmemCap = 227 * 1024 - 1024;   // dynamic shared memory, less alignment slack
 constexpr int kExactAcc1 = 256;                  // EXACT: TMEM column of accumulator 1
 constexpr int kSigRing = 8;                      // EXACT: row scales in flight
 
@@ -92,13 +95,26 @@ __device__ __forceinline__ void shift_ff(float x, float ohi, float olo, float& y
 }
 
 // Mode constants.
+// TF32X3 and BF16X3 stage 64-byte rows (64-byte swizzle); EXACT stages
+// 32-byte rows (32-byte swizzle, 16 K columns, one MMA K step per stage), so
+// that its four operand parts still leave room for five stages.
 template <int kMode> struct MC {
   static constexpr int kParts = kMode == M_EXACT ? 4 : 2;  // A/B operand parts
-  static constexpr int kKs = kMode == M_TF32 ? 16 : 32;    // K columns per stage
+  static constexpr int kKs = kMode == M_BF16 ? 32 : 16;    // K columns per stage
   static constexpr int kEl = kMode == M_TF32 ? 4 : 2;      // bytes per element
   static constexpr int kMmaK = kMode == M_TF32 ? 8 : 16;   // K per MMA
   static constexpr uint32_t kFmt = kMode == M_TF32 ? 2u : 1u;
+  static constexpr int kRow = kMode == M_EXACT ? 32 : 64;  // bytes of a part's row
+  static constexpr int kPart = kTileM * kRow;              // bytes of an A part
 };
+template <int kMode>
+__host__ __device__ __forceinline__ uint32_t swz_m(uint32_t row, uint32_t byte_in_row) {
+  return kMode == M_EXACT ? swz32(row, byte_in_row) : swz64(row, byte_in_row);
+}
+template <int kMode>
+__device__ __forceinline__ uint64_t sdesc_m(uint32_t saddr) {
+  return kMode == M_EXACT ? sdesc_sw32(saddr) : sdesc_sw64(saddr);
+}
 
 struct MmaArgs {
   Tables tb;
@@ -284,6 +300,7 @@ struct Smem {
   volatile int* abort_flag;
   double *rowG, *rowD2;
   float* rowSig;
+  float* rowMx;  // EXACT: max_j |x_j - o_j| of each row
   int* tabS;
   float *tabH, *tabL;
   int* item;  // persistent kernel: the work item of the CTA
@@ -304,10 +321,11 @@ __device__ inline Smem smem_map(uint8_t* smem_raw, int nstage, int stage_bytes) 
   m.tmem_slot = reinterpret_cast<uint32_t*>(m.gbar + nstage);
   m.abort_flag = reinterpret_cast<volatile int*>(m.tmem_slot + 1);
   m.item = const_cast<int*>(reinterpret_cast<volatile int*>(m.abort_flag) + 1);
-  m.rowG = reinterpret_cast<double*>(ctrl + 256);                 // [kMaxComponents][128]
-  m.rowD2 = m.rowG + kMaxComponents * kTileM;                     // [kMaxComponents][128]
-  m.rowSig = reinterpret_cast<float*>(m.rowD2 + kMaxComponents * kTileM);  // [kSigRing][128]
-  m.tabS = reinterpret_cast<int*>(m.rowSig + kSigRing * kTileM);           // [kMaxNpad]
+  m.rowG = reinterpret_cast<double*>(ctrl + kCtrlHeader);         // [kMaxComponents][128]
+  m.rowD2 = m.rowG + kMaxComponents * kTileM;                     // [2][kMaxComponents][128]
+  m.rowSig = reinterpret_cast<float*>(m.rowD2 + 2 * kMaxComponents * kTileM);  // [kSigRing][128]
+  m.rowMx = m.rowSig + kSigRing * kTileM;                         // [128]
+  m.tabS = reinterpret_cast<int*>(m.rowMx + kTileM);              // [kMaxNpad]
   m.tabH = reinterpret_cast<float*>(m.tabS + kMaxNpad);
   m.tabL = m.tabH + kMaxNpad;
   return m;
@@ -319,24 +337,25 @@ struct RoleState {
   uint32_t chunk_it = 0;  // accumulator hand-offs
   uint32_t pphase = 0;    // producer group barrier uses
   uint32_t comp_it = 0;   // components (row-scale ring)
+  uint32_t b_par = 0;     // B loads: bit s = parity of stage s's last load, bit 8 + s = used
 };
 
 __device__ inline void cta_setup(const Smem& m, int nstage) {
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     for (int s = 0; s < nstage; ++s) {
-      mbar_init(&m.full[s], 5);   // 4 producer warps + the B loader's expect_tx
+      mbar_init(&m.full[s], 9);   // 8 producer warps + the B loader's expect_tx
       mbar_init(&m.empty[s], 1);  // one tcgen05.commit
-      mbar_init(&m.gbar[s], 128); // producer threads' cp.async
+      mbar_init(&m.gbar[s], 256); // producer threads' cp.async
     }
     mbar_init(m.tmem_full, 1);
     mbar_init(m.tmem_empty, 4);   // the 4 epilogue warps
-    for (int s = 0; s < kSigRing; ++s) mbar_init(&m.sig_full[s], 4);
-    mbar_init(m.prod_bar, 4);     // the 4 producer warps
+    for (int s = 0; s < kSigRing; ++s) mbar_init(&m.sig_full[s], 4);  // producer warps 0-3
+    mbar_init(m.prod_bar, 8);     // the 8 producer warps
     *m.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 8) {
+  if (warp == kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(m.tmem_slot)),
                  "r"(kMaxNpad));
@@ -351,8 +370,8 @@ __device__ inline void cta_setup(const Smem& m, int nstage) {
 // tile (after a CTA barrier).
 __device__ inline void write_outputs(const MmaArgs& a, const Smem& m, long long row0) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp < 4 || warp >= 8 || *m.abort_flag) return;
-  const int r = (warp - 4) * 32 + lane;
+  if (warp < 8 || warp >= 12 || *m.abort_flag) return;
+  const int r = (warp - 8) * 32 + lane;
   const long long grow = row0 + r;
   if (grow >= a.N) return;
   const Function& F = a.F;
@@ -361,7 +380,7 @@ __device__ inline void write_outputs(const MmaArgs& a, const Smem& m, long long 
     double G[kMaxComponents], d2v[kMaxComponents];
     for (int ci = 0; ci < F.ncomp; ++ci) {
       G[ci] = m.rowG[ci * kTileM + r];
-      d2v[ci] = m.rowD2[ci * kTileM + r];
+      d2v[ci] = m.rowD2[ci * kTileM + r] + m.rowD2[(kMaxComponents + ci) * kTileM + r];
     }
     f = compose(a.tb.comp + F.comp0, F.ncomp, G, d2v, a.tb.D);
   } else {
@@ -372,7 +391,7 @@ __device__ inline void write_outputs(const MmaArgs& a, const Smem& m, long long 
 
 __device__ inline void cta_teardown(const Smem& m) {
   const int warp = threadIdx.x >> 5;
-  if (warp == 8) {
+  if (warp == kMmaWarp) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*m.tmem_slot),
                  "r"(kMaxNpad));
@@ -383,7 +402,8 @@ __device__ inline void cta_teardown(const Smem& m) {
   using C = MC<kMode>;                                                        \
   constexpr int kKs = C::kKs, kEl = C::kEl, kParts = C::kParts;               \
   constexpr int kKsteps = kKs / C::kMmaK;                                     \
-  (void)kEl; (void)kParts; (void)kKsteps;                                     \
+  constexpr int kRow = C::kRow, kPart = C::kPart;                             \
+  (void)kEl; (void)kParts; (void)kKsteps; (void)kRow; (void)kPart;            \
   const Tables& tb = a.tb;                                                    \
   const Function& F = a.F;                                                    \
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;                 \
@@ -408,19 +428,35 @@ template <int kMode>
 __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, RoleState& rs) {
   CUROB_ROLE_PROLOGUE
     // ------------------------------------------------------------ producers
-    // Thread = candidate row r.  The raw x values of a K stage are gathered
-    // with 4-byte cp.async straight into the stage's own A area (row r only:
-    // the first 64 bytes of part 0's row r, then part 1's), nstage - 1 stages
-    // ahead; converting a stage reads the thread's own raw row back, then
-    // overwrites that row of every part, so no other thread is involved.
-    const int r = warp * 32 + lane;
+    // Eight warps: warp w takes rows 32 (w % 4) .. + 31 (thread = candidate
+    // row r) and half h = w / 4 of every stage's K columns, so two warps
+    // share each row.  The raw x of a stage is gathered with 4-byte cp.async
+    // straight into the A area, each half's values into the very 16-byte
+    // chunks that half will overwrite with its converted operands: a thread
+    // reads only its own raw values back, and no other thread touches them.
+    const int h = warp >> 2;                 // half of the stage's columns
+    const int r = (warp & 3) * 32 + lane;    // candidate row in the tile
+    constexpr int kHalf = kKs / 2;           // columns per half
+    constexpr int kCpp = kRow / 32;          // 16-byte chunks per part row per half
     const long long grow = row0 + r;
     const bool vrow = grow < a.N;
     const float* xrow = a.x + (vrow ? grow : 0) * (long long)D;
-    const int P = a.nstage - 1;  // gather prefetch depth (stages)
+    // Gather prefetch depth: the gather of stage q + P goes into the A area
+    // of stage q + P - nstage, whose MMAs retired (nstage >= 3: P = nstage -
+    // 2, issued before stage q is converted, so it never waits on the MMAs
+    // of the stage just handed over).
+    const bool early = a.nstage >= 3;
+    const int P = early ? a.nstage - 2 : 1;
     uint32_t& it = rs.it;
     uint32_t& pphase = rs.pphase;
     bool ok = true;
+    if (vrow && h == 0) {  // bring the row into L2 now: the gathers then wait on L2, not HBM
+      const uintptr_t s0 = (reinterpret_cast<uintptr_t>(xrow) + 15) & ~uintptr_t(15);
+      const uintptr_t s1 = reinterpret_cast<uintptr_t>(xrow + D) & ~uintptr_t(15);
+      if (s1 > s0)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s0), "r"((uint32_t)(s1 - s0))
+                     : "memory");
+    }
     for (int ci = 0; ci < F.ncomp && ok; ++ci, ++rs.comp_it) {
       const uint32_t cg = rs.comp_it;  // component counter across tiles
       const Component Cm = tb.comp[F.comp0 + ci];
@@ -430,38 +466,56 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
       double d2 = 0.0;
       float isig = 1.f;
       if constexpr (kMode == M_EXACT) {
-        // row scale sigma_m = 2^e > max_j |x_j - o_j| over the component,
-        // read in natural order (contiguous row, o as FP32)
-        float mx = 0.f;
-        if (vrow) {
-          const float* on = a.onat + Cm.base;
-          int k = 0;
-          if ((D & 3) == 0) {
-            const float4* x4 = reinterpret_cast<const float4*>(xrow);
-            const float4* o4 = reinterpret_cast<const float4*>(on);
+        // max_j |x_j - o_j| of each row over the component, read in natural
+        // order: half h of the warp pair reads rows 16 h .. 16 h + 15 of the
+        // pair's 32 with coalesced loads (o as FP32); the maxima meet in
+        // rowMx and are read after the next producer barrier
+        const float* on = a.onat + Cm.base;
+        const bool vec = (D & 3) == 0 && (reinterpret_cast<uintptr_t>(a.x) & 15u) == 0;
+#pragma unroll 2
+        for (int rr = 16 * h; rr < 16 * h + 16; ++rr) {
+          const int row = (warp & 3) * 32 + rr;
+          const long long gr = row0 + row;
+          float mv = 0.f;
+          if (gr < a.N) {  // uniform across the warp
+            const float* xr_ = a.x + gr * (long long)D;
+            if (vec) {
+              const float4* x4 = reinterpret_cast<const float4*>(xr_);
+              const float4* o4 = reinterpret_cast<const float4*>(on);
 #pragma unroll 4
-            for (; k < D / 4; ++k) {
-              const float4 a = __ldg(x4 + k), b = __ldg(o4 + k);
-              mx = fmaxf(mx, fmaxf(fmaxf(fabsf(a.x - b.x), fabsf(a.y - b.y)),
-                                   fmaxf(fabsf(a.z - b.z), fabsf(a.w - b.w))));
+              for (int k4 = lane; k4 < D / 4; k4 += 32) {
+                const float4 u = __ldg(x4 + k4), w = __ldg(o4 + k4);
+                mv = fmaxf(mv, fmaxf(fmaxf(fabsf(u.x - w.x), fabsf(u.y - w.y)),
+                                     fmaxf(fabsf(u.z - w.z), fabsf(u.w - w.w))));
+              }
+            } else {
+              for (int k = lane; k < D; k += 32) mv = fmaxf(mv, fabsf(__ldg(xr_ + k) - on[k]));
             }
-            k *= 4;
           }
-          for (; k < D; ++k) mx = fmaxf(mx, fabsf(__ldg(xrow + k) - on[k]));
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) mv = fmaxf(mv, __shfl_xor_sync(0xffffffffu, mv, off));
+          if (lane == 0) m.rowMx[row] = mv;
         }
-        int e = 0;
-        if (mx > 0.f && mx < 3.0e38f) e = ilogbf(mx * 1.0009765625f) + 1;
-        isig = ldexpf(1.f, -e);
-        rowSig[(cg % kSigRing) * kTileM + r] = ldexpf(1.f, e);
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&sig_full[cg % kSigRing]);
       }
       for (int si = 0; si < Cm.nseg && ok; ++si) {
         const Segment sg = tb.seg[Cm.seg0 + si];
         // stage the block's index list and o words in shared memory (the
         // previous block's readers are done at the first barrier)
         if (!producers_sync(prod_bar, pphase, abort_flag, tb.status)) { ok = false; break; }
-        for (int k = r; k < sg.npad; k += kTileM) {
+        if constexpr (kMode == M_EXACT) {
+          if (si == 0) {  // row scale sigma_m = 2^e > the row's maximum
+            const float mx = m.rowMx[r];
+            int e = 0;
+            if (mx > 0.f && mx < 3.0e38f) e = ilogbf(mx * 1.0009765625f) + 1;
+            isig = ldexpf(1.f, -e);
+            if (h == 0) {
+              rowSig[(cg % kSigRing) * kTileM + r] = ldexpf(1.f, e);
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&sig_full[cg % kSigRing]);
+            }
+          }
+        }
+        for (int k = h * kTileM + r; k < sg.npad; k += 2 * kTileM) {
           const bool in = k < sg.n;
           tabS[k] = in ? S[sg.zoff + k] : 0;
           tabH[k] = in ? ohi[sg.zoff + k] : 0.f;
@@ -472,10 +526,11 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
         const int nchunk = kMode == M_EXACT ? exact_nchunk(sg.npad) : 1;
         const int total = nslab * nchunk;  // stages of this block
         const uint32_t it0 = it;
-        // raw x of stage q, row rr: kKs floats at part 0 row rr (first 16)
-        // and part 1 row rr (next 16).  Lanes walk a row's (sorted) columns,
-        // so one instruction touches one or two rows' few sectors; each
-        // thread's copies arrive on gbar[stage] when they land.
+        // raw x of stage q: half h's column i goes to 16-byte chunk
+        // (h kCpp + (i / 4) % kCpp) of part (i / 4) / kCpp of the row, in the
+        // operand's swizzle.  Lanes walk rows' (sorted) columns, so one
+        // instruction touches a few rows' few sectors; each thread's copies
+        // arrive on gbar[stage] when they land.
         const float* xbase = a.x;
         const long long nrows = a.N;
         const int nst = a.nstage, sbytes = a.stage_bytes, nvalid = sg.n;
@@ -486,20 +541,20 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
             return false;
           uint8_t* A = stages + (size_t)stage * sbytes;
           const int t = q % nslab;
-          constexpr int kRowsPerInst = 32 / kKs;            // 2 (TF32) or 1
-          const int k = lane % kKs;                         // column of the stage
-          const int j = t * kKs + k;
+          constexpr int kRowsPerInst = 32 / kHalf;          // 4 (16-column stages) or 2
+          const int i = lane % kHalf;                       // column of the half
+          const int j = t * kKs + h * kHalf + i;
           const bool cin = j < nvalid;
           const int col = cin ? tabS[j] : 0;
-          const uint32_t dcol = (uint32_t)((k >> 4) * kPartBytes + (k & 15) * 4);
-          const uint32_t dbase = smem_u32(A) + dcol;
+          const uint32_t dpart = smem_u32(A) + (uint32_t)(((i / 4) / kCpp) * kPart);
+          const uint32_t dbyte = (uint32_t)((h * kCpp + (i / 4) % kCpp) * 16 + (i % 4) * 4);
 #pragma unroll 4
-          for (int i = 0; i < 32 / kRowsPerInst; ++i) {
-            const int rr = warp * 32 + i * kRowsPerInst + lane / kKs;
+          for (int v = 0; v < 32 / kRowsPerInst; ++v) {
+            const int rr = (warp & 3) * 32 + v * kRowsPerInst + lane / kHalf;
             const long long gr = row0 + rr;
             const bool in = cin && gr < nrows;
             const float* src = in ? xbase + gr * (long long)D + col : xbase;
-            const uint32_t dst = dbase + (uint32_t)(rr * kRowBytes);
+            const uint32_t dst = dpart + swz_m<kMode>((uint32_t)rr, dbyte);
             asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src),
                          "r"(in ? 4 : 0)
                          : "memory");
@@ -512,40 +567,49 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
         const int npre = min(P, total);
         for (int q = 0; q < npre && ok; ++q) ok = issue(q);
         for (int q = 0; q < total && ok; ++q, ++it) {
-          if (!mbar_wait(&gbar[it % a.nstage], (it / a.nstage) & 1u, abort_flag, tb.status)) {
-            ok = false;
-            break;
-          }
           const int stage = it % a.nstage;
           uint8_t* A = stages + (size_t)stage * a.stage_bytes;
           const int t = q % nslab;
-          // the row's raw x of this stage, read before any part is overwritten
-          float4 xr[kKs / 4];
+          if (!mbar_wait(&gbar[stage], (it / a.nstage) & 1u, abort_flag, tb.status)) {
+            ok = false;
+            break;
+          }
+          if (early && q + P < total && !issue(q + P)) {
+            ok = false;
+            break;
+          }
+          // the row's raw x of this half-stage, read before it is overwritten
+          float xv[kHalf];
 #pragma unroll
-          for (int k = 0; k < kKs; k += 4)
-            xr[k / 4] = *reinterpret_cast<const float4*>(A + (k >> 4) * kPartBytes +
-                                                         r * kRowBytes + (k & 15) * 4);
+          for (int i4 = 0; i4 < kHalf / 4; ++i4) {
+            const float4 q4 = *reinterpret_cast<const float4*>(
+                A + (i4 / kCpp) * kPart +
+                swz_m<kMode>((uint32_t)r, (uint32_t)((h * kCpp + i4 % kCpp) * 16)));
+            xv[4 * i4] = q4.x;
+            xv[4 * i4 + 1] = q4.y;
+            xv[4 * i4 + 2] = q4.z;
+            xv[4 * i4 + 3] = q4.w;
+          }
           constexpr int kPer = 16 / kEl;  // elements per 16-byte chunk
           float d2p = 0.f;
-          // one 64-byte row per part = four 16-byte chunks, each stored whole
+          // this half's kCpp chunks of 16 bytes per part row, each stored whole
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
+          for (int cc = 0; cc < kCpp; ++cc) {
+            const int c = h * kCpp + cc;  // chunk of the row
             float yh[kPer], yl[kPer];
 #pragma unroll
             for (int e = 0; e < kPer; ++e) {
-              const int k = c * kPer + e;
-              const int j = t * kKs + k;
-              const float4 q4 = xr[k / 4];
-              const float xv = (k & 3) == 0 ? q4.x : (k & 3) == 1 ? q4.y : (k & 3) == 2 ? q4.z : q4.w;
-              if (vrow && j < sg.n) {
-                shift_ff(xv, tabH[j], tabL[j], yh[e], yl[e]);
-              } else {
-                yh[e] = 0.f;
-                yl[e] = 0.f;
-              }
+              const int il = cc * kPer + e;  // column within the half
+              const int j = t * kKs + h * kHalf + il;
+              // branch-free, so that the chunk's elements interleave
+              float hh, ll;
+              shift_ff(xv[il], tabH[j], tabL[j], hh, ll);
+              const bool valid = vrow && j < nvalid;
+              yh[e] = valid ? hh : 0.f;
+              yl[e] = valid ? ll : 0.f;
               d2p = fmaf(yh[e], yh[e], d2p);
             }
-            const uint32_t off = swz64((uint32_t)r, (uint32_t)(c * 16));
+            const uint32_t off = swz_m<kMode>((uint32_t)r, (uint32_t)(c * 16));
             if constexpr (kMode == M_TF32) {
               uint32_t hw[4], lw[4];
 #pragma unroll
@@ -555,7 +619,7 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
                 lw[qq] = to_tf32((a - __uint_as_float(hw[qq])) + yl[qq]);
               }
               *reinterpret_cast<uint4*>(A + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-              *reinterpret_cast<uint4*>(A + kPartBytes + off) =
+              *reinterpret_cast<uint4*>(A + kPart + off) =
                   make_uint4(lw[0], lw[1], lw[2], lw[3]);
             } else if constexpr (kMode == M_BF16) {
               uint32_t hw[4], lw[4];
@@ -567,7 +631,7 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
                 lw[qq] = pack_bf16((a - hf.x) + yl[2 * qq], (b - hf.y) + yl[2 * qq + 1]);
               }
               *reinterpret_cast<uint4*>(A + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-              *reinterpret_cast<uint4*>(A + kPartBytes + off) =
+              *reinterpret_cast<uint4*>(A + kPart + off) =
                   make_uint4(lw[0], lw[1], lw[2], lw[3]);
             } else {
               // four integer slices of 128 y / sigma (exact in BF16),
@@ -596,7 +660,7 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
               }
 #pragma unroll
               for (int pp = 0; pp < 4; ++pp)
-                *reinterpret_cast<uint4*>(A + pp * kPartBytes + off) =
+                *reinterpret_cast<uint4*>(A + pp * kPart + off) =
                     make_uint4(w[pp][0], w[pp][1], w[pp][2], w[pp][3]);
             }
           }
@@ -604,10 +668,10 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
           fence_proxy_async();
           __syncwarp();
           if (lane == 0) mbar_arrive(&full[stage]);
-          if (q + P < total) ok = issue(q + P);
+          if (!early && q + P < total) ok = issue(q + P);
         }
       }
-      rowD2[ci * kTileM + r] = d2;
+      rowD2[(h * kMaxComponents + ci) * kTileM + r] = d2;  // each half's share
     }
 }
 
@@ -616,7 +680,7 @@ __device__ void epilogue_tile(const MmaArgs& a, const Smem& m, long long row0, R
   CUROB_ROLE_PROLOGUE
   (void)row0;
     // ------------------------------------------------------------- epilogue
-    const int q = warp - 4;                 // TMEM lane quadrant
+    const int q = warp - 8;                 // TMEM lane quadrant (warp % 4)
     const int r = q * 32 + lane;            // candidate row in the tile
     const uint32_t t_lane = tmem_base + ((uint32_t)(q * 32) << 16);
     uint32_t& chunk_it = rs.chunk_it;
@@ -718,11 +782,11 @@ __device__ void mma_tile(const MmaArgs& a, const Smem& m, long long row0, RoleSt
               }
               tc_fence_after();
               const uint32_t sa = smem_u32(stages + (size_t)stage * a.stage_bytes);
-              const uint32_t sb = sa + kParts * kPartBytes;
-              const uint32_t bpart = (uint32_t)(nc * kRowBytes);
+              const uint32_t sb = sa + kParts * kPart;
+              const uint32_t bpart = (uint32_t)(nc * kRow);
 #pragma unroll
               for (int kk = 0; kk < kKsteps; ++kk) {
-                const uint32_t ko = (uint32_t)(kk * C::kMmaK * kEl);  // 32 B per K step
+                const uint32_t ko = (uint32_t)(kk * C::kMmaK * kEl);  // bytes per K step
                 const uint32_t first = (t == 0 && kk == 0) ? 0u : 1u;
                 if constexpr (kMode == M_EXACT) {
                   // s1 r1 into accumulator 0; the pre-scaled products of
@@ -732,15 +796,15 @@ __device__ void mma_tile(const MmaArgs& a, const Smem& m, long long row0, RoleSt
 #pragma unroll
                   for (int pq = 0; pq < 10; ++pq) {
                     const uint32_t dt = tmem_base + (pq == 0 ? 0u : (uint32_t)kExactAcc1);
-                    const uint64_t da = sdesc_sw64(sa + kPa[pq] * kPartBytes + ko);
-                    const uint64_t db = sdesc_sw64(sb + kPb[pq] * bpart + ko);
+                    const uint64_t da = sdesc_m<kMode>(sa + kPa[pq] * kPart + ko);
+                    const uint64_t db = sdesc_m<kMode>(sb + kPb[pq] * bpart + ko);
                     tc_mma<false>(dt, da, db, id0, (pq <= 1) ? first : 1u);
                   }
                 } else {
-                  const uint64_t dah = sdesc_sw64(sa + ko), dal = sdesc_sw64(sa + kPartBytes + ko);
+                  const uint64_t dah = sdesc_m<kMode>(sa + ko), dal = sdesc_m<kMode>(sa + kPart + ko);
                   for (int h = 0; h < (n1 > 0 ? 2 : 1); ++h) {
-                    const uint32_t boff = (uint32_t)(h * n0 * kRowBytes) + ko;
-                    const uint64_t dbh = sdesc_sw64(sb + boff), dbl = sdesc_sw64(sb + bpart + boff);
+                    const uint32_t boff = (uint32_t)(h * n0 * kRow) + ko;
+                    const uint64_t dbh = sdesc_m<kMode>(sb + boff), dbl = sdesc_m<kMode>(sb + bpart + boff);
                     const uint32_t dt = tmem_base + (uint32_t)(h * n0);
                     const uint32_t idd = h ? id1 : id0;
                     tc_mma<kMode == M_TF32>(dt, dah, dbh, idd, first);
@@ -778,8 +842,8 @@ __device__ void loader_tile(const MmaArgs& a, const Smem& m, long long row0, Rol
           const uint8_t* base = a.img + ((size_t)sg.img_off + (size_t)kMode * fl) * 4;
           for (int cc = 0; cc < nchunk && ok; ++cc) {
             const int nc = kMode == M_EXACT ? min(nw, sg.npad - cc * nw) : sg.npad;
-            const uint32_t bytes = (uint32_t)(kParts * nc * kRowBytes);
-            const uint8_t* src = base + (size_t)cc * nslab * kParts * nw * kRowBytes;
+            const uint32_t bytes = (uint32_t)(kParts * nc * kRow);
+            const uint8_t* src = base + (size_t)cc * nslab * kParts * nw * kRow;
             for (int t = 0; t < nslab; ++t, ++it) {
               const int stage = it % a.nstage;
               const uint32_t ph = (it / a.nstage) & 1u;
@@ -787,8 +851,9 @@ __device__ void loader_tile(const MmaArgs& a, const Smem& m, long long row0, Rol
                 ok = false;
                 break;
               }
-              uint8_t* dst = stages + (size_t)stage * a.stage_bytes + kParts * kPartBytes;
+              uint8_t* dst = stages + (size_t)stage * a.stage_bytes + kParts * kPart;
               mbar_arrive_expect_tx(&full[stage], bytes);
+              rs.b_par = (rs.b_par & ~(1u << stage)) | (ph << stage) | (1u << (stage + 8));
               bulk_g2s(dst, src + (size_t)t * bytes, bytes, &full[stage]);
             }
           }
@@ -801,10 +866,17 @@ __device__ void loader_tile(const MmaArgs& a, const Smem& m, long long row0, Rol
 template <int kMode>
 __device__ inline void run_tile(const MmaArgs& a, const Smem& m, long long row0, RoleState& rs) {
   const int warp = threadIdx.x >> 5;
-  if (warp < 4) producer_tile<kMode>(a, m, row0, rs);
-  else if (warp < 8) epilogue_tile<kMode>(a, m, row0, rs);
-  else if (warp == 8) mma_tile<kMode>(a, m, row0, rs);
+  if (warp < 8) producer_tile<kMode>(a, m, row0, rs);
+  else if (warp < 12) epilogue_tile<kMode>(a, m, row0, rs);
+  else if (warp == kMmaWarp) mma_tile<kMode>(a, m, row0, rs);
   else loader_tile<kMode>(a, m, row0, rs);
+  if (*m.abort_flag) {  // no copy may still be landing when the CTA moves on or exits
+    const unsigned long long deadline = globaltimer() + kTimeoutNs;
+    if (warp < 8) asm volatile("cp.async.wait_all;" ::: "memory");
+    if (warp == kLoaderWarp && (threadIdx.x & 31) == 0)
+      for (int s = 0; s < a.nstage; ++s)
+        if (rs.b_par >> (s + 8) & 1u) mbar_drain(&m.full[s], rs.b_par >> s & 1u, deadline);
+  }
   // every issued MMA has been consumed by the epilogue (or the CTA aborted)
   tc_fence_before();
   __syncthreads();
@@ -881,7 +953,6 @@ __global__ void build_image_kernel(const ImgJob* jobs, const double* R, uint8_t*
     tau[J.tau_off + row] = ldexpf(1.f, e);
   }
   __syncthreads();
-  const int nslab32 = npad / 32;
   const long long total = (long long)npad * npad;
   for (long long e = threadIdx.x; e < total; e += blockDim.x) {
     const int row = (int)(e / npad), col = (int)(e - (long long)row * npad);
@@ -906,19 +977,20 @@ __global__ void build_image_kernel(const ImgJob* jobs, const double* R, uint8_t*
       *reinterpret_cast<__nv_bfloat16*>(hi + off) = h;
       *reinterpret_cast<__nv_bfloat16*>(lo + off) = l;
     }
-    {  // EXACT: chunk cc = row / nw, stage t = col / 32, four pre-scaled slices
+    {  // EXACT: chunk cc = row / nw, stage t = col / 16 (32-byte rows), four slices
       const int nw = exact_nw(npad);
       const int cc = row / nw, rr = row % nw;
       const int nc = min(nw, npad - cc * nw);
-      const int t = col / 32, k = col % 32;
+      const int t = col / 16, k = col % 16;
+      const int nslab16 = npad / 16;
       uint8_t* st = base + (size_t)2 * fl * 4 +
-                    ((size_t)cc * nslab32 * 4 * nw + (size_t)t * 4 * nc) * kRowBytes;
-      const uint32_t off = swz64((uint32_t)rr, (uint32_t)(k * 2));
+                    ((size_t)cc * nslab16 * 4 * nw + (size_t)t * 4 * nc) * 32;
+      const uint32_t off = swz32((uint32_t)rr, (uint32_t)(k * 2));
       double w = v / (double)tau[J.tau_off + row] * 128.0;  // exact: tau is 2^f
       double scale = 1.0;
       for (int s = 0; s < 4; ++s) {
         const double yv = rint(w);
-        *reinterpret_cast<__nv_bfloat16*>(st + (size_t)s * nc * kRowBytes + off) =
+        *reinterpret_cast<__nv_bfloat16*>(st + (size_t)s * nc * 32 + off) =
             __double2bfloat16(yv * scale);
         w = (w - yv) * 256.0;
         scale *= 0.00390625;
@@ -943,10 +1015,12 @@ int npad_of(int n) { return (n + 31) / 32 * 32; }
 
 template <int kMode>
 size_t stage_bytes_for(int ncmax) {
-  return (size_t)MC<kMode>::kParts * kPartBytes + (size_t)MC<kMode>::kParts * ncmax * kRowBytes;
+  return (size_t)MC<kMode>::kParts * MC<kMode>::kPart +
+         (size_t)MC<kMode>::kParts * ncmax * MC<kMode>::kRow;
 }
 size_t ctrl_bytes() {  // barriers and work item (<= 256 B) + per-row tables + block table
-  return 256 + 2 * sizeof(double) * kMaxComponents * kTileM + sizeof(float) * kSigRing * kTileM +
+  return kCtrlHeader + 3 * sizeof(double) * kMaxComponents * kTileM +
+         sizeof(float) * (kSigRing + 1) * kTileM +
          3 * sizeof(float) * kMaxNpad;
 }
 
@@ -957,7 +1031,7 @@ cudaError_t launch_mode(const MmaPlan& p, const Tables& tb, const Function& F, c
   const int ncmax = kMode == M_EXACT ? std::min(npad_max, kExactMaxNC) : npad_max;
   const size_t sb = stage_bytes_for<kMode>(ncmax);
   const size_t ctrl = ctrl_bytes();
-  const int nstage = (int)std::min<size_t>(4, (219 * 1024 - ctrl) / sb);
+  const int nstage = (int)std::min<size_t>(kMaxStages, (kSmemCap - ctrl) / sb);
   if (nstage < 2) return cudaErrorInvalidValue;
   const size_t smem = nstage * sb + ctrl + 1024;  // + alignment slack
   MmaArgs a;
@@ -1098,7 +1172,7 @@ BatchGeom batch_geom() {
   BatchGeom g;
   const size_t sb = stage_bytes_for<M_EXACT>(kExactMaxNC);
   g.stage_bytes = (int)sb;
-  g.nstage = (int)std::min<size_t>(4, (219 * 1024 - ctrl_bytes()) / sb);
+  g.nstage = (int)std::min<size_t>(kMaxStages, (kSmemCap - ctrl_bytes()) / sb);
   g.smem = g.nstage * sb + ctrl_bytes() + 1024;
   return g;
 }

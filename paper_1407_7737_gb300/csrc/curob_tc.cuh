@@ -63,6 +63,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   }
   return true;
 }
+// Waits, until `deadline` (globaltimer ns) and whatever the abort flag says,
+// for the phase of `parity` (used on the abort path, so that no copy is
+// still landing in shared memory when the CTA exits).
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity,
+                                           unsigned long long deadline) {
+  while (!mbar_try_wait(bar, parity))
+    if (globaltimer() > deadline) break;
+}
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -140,6 +148,17 @@ __device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
   d |= (uint64_t)4u << 61;                       // SWIZZLE_64B
   return d;
 }
+// The same for 32-byte-swizzled K-major rows of 32 B: 8-row groups 256 B
+// apart (SBO), layout type 6.
+__device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;                       // LBO (unused for swizzled K-major)
+  d |= (uint64_t)((256u >> 4) & 0x3FFFu) << 32;  // SBO
+  d |= (uint64_t)1u << 46;                       // version
+  d |= (uint64_t)6u << 61;                       // SWIZZLE_32B
+  return d;
+}
 // Instruction descriptor: FP32 accumulator, A/B format (TF32 = 2, BF16 = 1),
 // both K-major, N >> 3, M >> 4.
 __host__ __device__ constexpr uint32_t idesc_make(uint32_t fmt, uint32_t M, uint32_t N) {
@@ -151,6 +170,13 @@ __host__ __device__ constexpr uint32_t idesc_make(uint32_t fmt, uint32_t M, uint
 __host__ __device__ __forceinline__ uint32_t swz64(uint32_t row, uint32_t byte_in_row) {
   uint32_t off = row * kRowBytes + byte_in_row;
   return off ^ (((off >> 7) & 3u) << 4);
+}
+
+// Byte offset of (row, byte-in-row) in the 32-byte-swizzled image of 32-byte
+// rows: the 16-byte chunk index (bit 4) XOR bit 7 of the linear offset.
+__host__ __device__ __forceinline__ uint32_t swz32(uint32_t row, uint32_t byte_in_row) {
+  uint32_t off = row * 32u + byte_in_row;
+  return off ^ (((off >> 7) & 1u) << 4);
 }
 
 __device__ __forceinline__ uint32_t to_tf32(float v) {
