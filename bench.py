@@ -161,17 +161,6 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def algorithmic_flops(cu, fid):
-    """2 * sum_b n_b^2 per candidate over every rotated block of fid (the
-    contraction z_b = R_b y_b), the unit of the tensor roofline."""
-    total = 0
-    for c in range(cu.curob_num_components(fid)):
-        sizes, rot = cu.curob_component_layout(fid, c)
-        if rot:
-            total += 2 * sum(n * n for n in sizes)
-    return total
-
-
 def run_curob(args):
     import torch
     from paper_1407_7737_gb300 import binding as cu
@@ -279,41 +268,50 @@ def run_curob(args):
     if rank == 0 and not args.no_extra:
         ragged = ragged_batch(cu, torch, dev, stream, reps=max(3, args.steps))
 
-    # roofline of the dominant kernel (the tensor-core mode holding most of
-    # the step).  Its algorithmic work is 2 sum_b n_b^2 flops per candidate
-    # and rotated component; the peak is the rate of algorithmic products
-    # that mode can reach: TF32X3 runs 3 TF32 products per product, EXACT 10
-    # BF16 products, BF16X3 3 BF16 products.
+    # roofline of the dominant kernel group (the precision holding most of the
+    # step).  Algorithmic work: 2 sum_b n_b^2 flops per candidate and rotated
+    # component; each component's peak is the rate of algorithmic products its
+    # precision reaches (TF32X3: 3 TF32 products per product, EXACT: 10 BF16
+    # products).  A MIXED composition runs its members at their own
+    # precisions, so its peak is the members' blend: frac = (time the members
+    # would take at their peaks) / (measured time).
     pk, src = peaks()
-    flops = np.array([algorithmic_flops(cu, f) * N for f in range(NFUN)], dtype=np.float64)
-    modes_a = np.array(modes)
     bf16 = pk["bf16_tflops"]
-    mode_info = {
-        1: ("mma_eval_kernel<TF32X3>", bf16 * (1.1 / 2.25) / 3.0,
-            f"{src} bf16 burst x 1.1/2.25 (TF32/BF16 nominal ratio) / 3 TF32 products"),
-        2: ("mma_eval_kernel<BF16X3>", bf16 / 3.0, f"{src} bf16 burst / 3 BF16 products"),
-        4: ("mma_eval_kernel<EXACT>", bf16 / 10.0, f"{src} bf16 burst / 10 BF16 products"),
-        3: ("eval_simt_f32_kernel", 152 * 128 * 2 * 2.07e9 / 1e12 / 6.0,
-            "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz / ~6 ops per compensated product"),
-    }
+    mode_peak = {1: bf16 * (1.1 / 2.25) / 3.0, 2: bf16 / 3.0, 4: bf16 / 10.0,
+                 3: 152 * 128 * 2 * 2.07e9 / 1e12 / 6.0}
+    mode_name = {1: "mma_eval_kernel<TF32X3>", 2: "mma_eval_kernel<BF16X3>",
+                 4: "mma_eval_kernel<EXACT>", 3: "eval_simt_f32_kernel",
+                 5: "mma_eval_kernel<EXACT> + <TF32X3> (mixed compositions)"}
+    flops = np.zeros(NFUN)
+    t_bound = np.zeros(NFUN)  # seconds at the tensor peaks of the components' precisions
+    for f in range(NFUN):
+        for c in range(cu.curob_num_components(f)):
+            sizes, rot = cu.curob_component_layout(f, c)
+            if not rot:
+                continue
+            fl = 2.0 * sum(n * n for n in sizes) * N
+            flops[f] += fl
+            t_bound[f] += fl / (mode_peak[cu.curob_query_component_precision(f, c)] * 1e12)
+    modes_a = np.array(modes)
     share = {m: launch_ms[modes_a == m].sum() for m in set(modes)}
     dom = max(share, key=share.get)
     sel = (modes_a == dom) & (flops > 0)
     achieved = flops[sel].sum() / (launch_ms[sel].sum() / 1e3) / 1e12
-    kname, peak, psrc = mode_info[dom]
-    roof = {"bound": "tensor" if dom != 3 else "alu", "kernel": kname,
+    peak = flops[sel].sum() / t_bound[sel].sum() / 1e12
+    roof = {"bound": "tensor" if dom != 3 else "alu", "kernel": mode_name[dom],
             "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
             "frac": round(achieved / peak, 4), "traffic": None,
-            "peak_source": psrc, "share_of_step": round(share[dom] / launch_ms.sum(), 3),
+            "peak_source": f"{src} bf16 burst; per algorithmic product: EXACT / 10 BF16 products, "
+                           "TF32X3 x 1.1/2.25 (TF32/BF16 nominal ratio) / 3 TF32 products",
+            "share_of_step": round(share[dom] / launch_ms.sum(), 3),
             "launches_per_step": int(sel.sum()),
             "note": "achieved = algorithmic flops (2*sum n_b^2 per candidate and rotated "
-                    "component) / CUDA-event time of those launches"}
-    # per function: time against the tensor bound of its own mode and the
-    # HBM bound of reading x once (4 D + 4 bytes per candidate)
+                    "component) / CUDA-event time of those functions' calls"}
+    # per function: time against its tensor bound and the HBM bound of
+    # reading x once (4 D + 4 bytes per candidate)
     per_fn = []
     for f in range(NFUN):
-        pkm = mode_info[modes[f]][1]
-        t_tc = flops[f] / (pkm * 1e12) * 1e3
+        t_tc = t_bound[f] * 1e3
         t_hbm = (4.0 * D + 4.0) * N / (pk["hbm_gbs"] * 1e9) * 1e3
         per_fn.append({"fid": f, "ms": round(float(launch_ms[f]), 4),
                        "tensor_bound_ms": round(t_tc, 4), "hbm_bound_ms": round(t_hbm, 4),
@@ -361,8 +359,8 @@ def run_curob(args):
             "fp64_evals_s": round(fp64, 1) if fp64 else None,
             **extra,
             "per_function_ms": [round(v, 4) for v in launch_ms.tolist()],
-            "per_function_path": [{1: "tf32x3", 2: "bf16x3", 3: "simt", 4: "exact"}[m]
-                                  for m in modes],
+            "per_function_path": [{1: "tf32x3", 2: "bf16x3", 3: "simt", 4: "exact",
+                                   5: "mixed"}[m] for m in modes],
             "roofline": roof, "roofline_per_function": per_fn, "cpu_baseline": cpu, "e2e": e2e, "ragged_batch": ragged,
             "surrogate": surrogate, "clocks": clk.summary(), "gpu_launches": gpu_launches,
         }

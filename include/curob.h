@@ -59,13 +59,17 @@ typedef enum {
  * SIMT: FP32 CUDA cores with a compensated dot product.  AUTO (default):
  * EXACT for functions containing Discus, Weierstrass, expanded
  * Griewank-Rosenbrock or Katsuura (they magnify z errors), TF32X3 for the
- * rest; SIMT where a block is narrower than 16 or wider than 512. */
+ * rest; for a composition only some of whose members contain such a kind,
+ * MIXED: those members on EXACT, the others on TF32X3 (reported by
+ * curob_query_precision, not selectable); SIMT where a block is narrower
+ * than 16 or wider than 512. */
 typedef enum {
   CUROB_PRECISION_AUTO = 0,
   CUROB_PRECISION_TF32X3 = 1,
   CUROB_PRECISION_BF16X3 = 2,
   CUROB_PRECISION_SIMT = 3,
-  CUROB_PRECISION_EXACT = 4
+  CUROB_PRECISION_EXACT = 4,
+  CUROB_PRECISION_MIXED = 5
 } curob_precision;
 
 /* Number of functions (Table 1). */
@@ -109,10 +113,15 @@ curob_status curob_h_evaluatef(int fid, const float* x, int N, float* out);
 curob_status curob_set_precision(int mode);
 
 /* The precision curob_evaluatef will use for fid under the current setting
- * (AUTO resolved): CUROB_PRECISION_TF32X3, _BF16X3, _EXACT or _SIMT.
+ * (AUTO resolved): CUROB_PRECISION_TF32X3, _BF16X3, _EXACT, _MIXED or _SIMT.
  * Errors: NOT_INITIALIZED, INVALID_FID, INVALID_DIM, NULL_POINTER,
  * UNSUPPORTED (a forced tensor-core precision the instance cannot use). */
 curob_status curob_query_precision(int fid, int* mode);
+
+/* The precision component `comp` of fid runs at (the same as
+ * curob_query_precision except for MIXED compositions, where it is EXACT or
+ * TF32X3 per member).  INVALID_ARGUMENT for comp outside the function. */
+curob_status curob_query_component_precision(int fid, int comp, int* mode);
 
 /* Synchronise `stream` and report (then clear) a latched device-side error. */
 curob_status curob_get_device_status(curob_stream_t stream);

@@ -21,6 +21,7 @@ STATUS = {
 CODES = {v: k for k, v in STATUS.items()}
 
 PRECISION_AUTO, PRECISION_TF32X3, PRECISION_BF16X3, PRECISION_SIMT, PRECISION_EXACT = 0, 1, 2, 3, 4
+PRECISION_MIXED = 5  # reported for compositions whose members take different precisions
 NUM_FUNCTIONS = 37
 FOPT = 100.0
 
@@ -38,6 +39,7 @@ _SIGS = [
     ("curob_h_evaluatef", _I, [_I, _P, _I, _P]),
     ("curob_set_precision", _I, [_I]),
     ("curob_query_precision", _I, [_I, _P]),
+    ("curob_query_component_precision", _I, [_I, _I, _P]),
     ("curob_get_device_status", _I, [_P]),
     ("curob_status_string", ctypes.c_char_p, [_I]),
     ("curob_get_config", _I, [_P, _P]),
@@ -169,6 +171,12 @@ def curob_set_precision(mode, check=True):
 def curob_query_precision(fid):
     m = ctypes.c_int()
     _call("curob_query_precision", fid, ctypes.addressof(m))
+    return m.value
+
+
+def curob_query_component_precision(fid, comp):
+    m = ctypes.c_int()
+    _call("curob_query_component_precision", fid, comp, ctypes.addressof(m))
     return m.value
 
 

@@ -155,6 +155,8 @@ curob_status curob_evaluatef(int fid, const float* x, int N, float* out, curob_s
   cudaError_t e;
   if (mode == CUROB_PRECISION_SIMT)
     e = launch_simt_f32(tables(), F, x, N, out, (cudaStream_t)stream);
+  else if (mode == CUROB_PRECISION_MIXED)
+    e = launch_mma_mixed(g.inst.mma, tables(), F, x, N, out, (cudaStream_t)stream);
   else
     e = launch_mma(g.inst.mma, tables(), F, mode, x, N, out, (cudaStream_t)stream);
   return e == cudaSuccess ? CUROB_OK : CUROB_ERR_CUDA;
@@ -204,6 +206,18 @@ curob_status curob_query_precision(int fid, int* mode) {
   if (!mode) return CUROB_ERR_NULL_POINTER;
   const int m = resolve_precision(g.inst.func[fid]);
   if (m < 0) return CUROB_ERR_UNSUPPORTED;
+  *mode = m;
+  return CUROB_OK;
+}
+
+curob_status curob_query_component_precision(int fid, int comp, int* mode) {
+  int m = 0;
+  curob_status rc = curob_query_precision(fid, &m);
+  if (rc != CUROB_OK) return rc;
+  const Function& F = g.inst.func[fid];
+  if (comp < 0 || comp >= F.ncomp) return CUROB_ERR_INVALID_ARGUMENT;
+  if (m == CUROB_PRECISION_MIXED)
+    m = (F.sens_mask >> comp & 1) ? CUROB_PRECISION_EXACT : CUROB_PRECISION_TF32X3;
   *mode = m;
   return CUROB_OK;
 }

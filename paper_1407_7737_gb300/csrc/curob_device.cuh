@@ -61,6 +61,7 @@ struct Function {
                       // Discus (10^6 z_1^2), Weierstrass (3^k phases),
                       // expanded Griewank-Rosenbrock (cos of g2 ~ 1e4),
                       // Katsuura (2^j phases)
+  int sens_mask;      // bit c: component c has such a kind
 };
 
 // Device view of an initialised instance.

@@ -134,6 +134,7 @@ void Instance::build_tables() {
     F.composition = fid >= 29;
     F.max_n = 0;
     F.sensitive = 0;
+    F.sens_mask = 0;
     for (int c = 0; c < ci.n; ++c) {
       const Member& m = ci.m[c];
       CompHost ch;
@@ -182,7 +183,10 @@ void Instance::build_tables() {
         s.npad = 0;
         s.comp = (int)comps.size();
         F.max_n = std::max(F.max_n, s.n);
-        if (kind_is_sensitive(s.kind)) F.sensitive = 1;
+        if (kind_is_sensitive(s.kind)) {
+          F.sensitive = 1;
+          F.sens_mask |= 1 << c;
+        }
         ch.segs.push_back((int)segs.size());
         segs.push_back(s);
       }

@@ -129,6 +129,10 @@ struct MmaArgs {
   const float* onat;     // EXACT: o per component in natural order, FP32
   int nstage;
   int stage_bytes;
+  int nlist;                   // components evaluated, in order (all of F's, or a subset)
+  int list[kMaxComponents];
+  double* gout;                // subset launches: G_c and ||x - o_c||^2 per component and row
+  double* d2out;               // ([kMaxComponents][N] each), composed by compose_kernel
 };
 
 // Floats reserved per block for each precision's image (the TF32 size; BF16
@@ -375,6 +379,15 @@ __device__ inline void write_outputs(const MmaArgs& a, const Smem& m, long long 
   const long long grow = row0 + r;
   if (grow >= a.N) return;
   const Function& F = a.F;
+  if (a.gout) {  // a subset of the components: their values for compose_kernel
+    for (int li = 0; li < a.nlist; ++li) {
+      const int ci = a.list[li];
+      a.gout[(size_t)ci * a.N + grow] = m.rowG[ci * kTileM + r];
+      a.d2out[(size_t)ci * a.N + grow] =
+          m.rowD2[ci * kTileM + r] + m.rowD2[(kMaxComponents + ci) * kTileM + r];
+    }
+    return;
+  }
   double f;
   if (F.composition) {
     double G[kMaxComponents], d2v[kMaxComponents];
@@ -457,7 +470,8 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s0), "r"((uint32_t)(s1 - s0))
                      : "memory");
     }
-    for (int ci = 0; ci < F.ncomp && ok; ++ci, ++rs.comp_it) {
+    for (int li = 0; li < a.nlist && ok; ++li, ++rs.comp_it) {
+      const int ci = a.list[li];
       const uint32_t cg = rs.comp_it;  // component counter across tiles
       const Component Cm = tb.comp[F.comp0 + ci];
       const int* S = tb.S + Cm.base;
@@ -685,7 +699,8 @@ __device__ void epilogue_tile(const MmaArgs& a, const Smem& m, long long row0, R
     const uint32_t t_lane = tmem_base + ((uint32_t)(q * 32) << 16);
     uint32_t& chunk_it = rs.chunk_it;
     EpiState st;
-    for (int ci = 0; ci < F.ncomp && !*abort_flag; ++ci, ++rs.comp_it) {
+    for (int li = 0; li < a.nlist && !*abort_flag; ++li, ++rs.comp_it) {
+      const int ci = a.list[li];
       const uint32_t cg = rs.comp_it;
       const Component Cm = tb.comp[F.comp0 + ci];
       double gsum = 0.0;
@@ -755,8 +770,8 @@ __device__ void mma_tile(const MmaArgs& a, const Smem& m, long long row0, RoleSt
       uint32_t& it = rs.it;
       uint32_t& chunk_it = rs.chunk_it;
       bool ok = true;
-      for (int ci = 0; ci < F.ncomp && ok && !*abort_flag; ++ci) {
-        const Component Cm = tb.comp[F.comp0 + ci];
+      for (int li = 0; li < a.nlist && ok && !*abort_flag; ++li) {
+        const Component Cm = tb.comp[F.comp0 + a.list[li]];
         for (int si = 0; si < Cm.nseg && ok; ++si) {
           const Segment sg = tb.seg[Cm.seg0 + si];
           const int nslab = sg.npad / kKs;
@@ -831,8 +846,8 @@ __device__ void loader_tile(const MmaArgs& a, const Smem& m, long long row0, Rol
     if (lane == 0) {
       uint32_t& it = rs.it;
       bool ok = true;
-      for (int ci = 0; ci < F.ncomp && ok && !*abort_flag; ++ci) {
-        const Component Cm = tb.comp[F.comp0 + ci];
+      for (int li = 0; li < a.nlist && ok && !*abort_flag; ++li) {
+        const Component Cm = tb.comp[F.comp0 + a.list[li]];
         for (int si = 0; si < Cm.nseg && ok; ++si) {
           const Segment sg = tb.seg[Cm.seg0 + si];
           const int nslab = sg.npad / kKs;
@@ -1024,9 +1039,24 @@ size_t ctrl_bytes() {  // barriers and work item (<= 256 B) + per-row tables + b
          3 * sizeof(float) * kMaxNpad;
 }
 
+// Composition (Sec. 6) of the per-component values that subset launches
+// wrote: one thread per candidate.
+__global__ void compose_kernel(Tables tb, Function F, const double* gout, const double* d2out,
+                               int N, float* out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double G[kMaxComponents], d2v[kMaxComponents];
+  for (int c = 0; c < F.ncomp; ++c) {
+    G[c] = gout[(size_t)c * N + i];
+    d2v[c] = d2out[(size_t)c * N + i];
+  }
+  out[i] = (float)(compose(tb.comp + F.comp0, F.ncomp, G, d2v, tb.D) + kFopt);
+}
+
 template <int kMode>
 cudaError_t launch_mode(const MmaPlan& p, const Tables& tb, const Function& F, const float* x,
-                        int N, float* out, cudaStream_t st) {
+                        int N, float* out, cudaStream_t st, const int* list = nullptr,
+                        int nlist = 0, double* gout = nullptr, double* d2out = nullptr) {
   const int npad_max = npad_of(F.max_n);
   const int ncmax = kMode == M_EXACT ? std::min(npad_max, kExactMaxNC) : npad_max;
   const size_t sb = stage_bytes_for<kMode>(ncmax);
@@ -1047,6 +1077,10 @@ cudaError_t launch_mode(const MmaPlan& p, const Tables& tb, const Function& F, c
   a.onat = p.onat;
   a.nstage = nstage;
   a.stage_bytes = (int)sb;
+  a.nlist = list ? nlist : F.ncomp;
+  for (int i = 0; i < kMaxComponents; ++i) a.list[i] = list ? (i < nlist ? list[i] : 0) : i;
+  a.gout = gout;
+  a.d2out = d2out;
   cudaError_t e = cudaFuncSetAttribute(mma_eval_kernel<kMode>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -1159,7 +1193,9 @@ bool mma_supports(const MmaPlan& p, const Function& F) {
 
 int mma_auto_mode(const MmaPlan& p, const Function& F) {
   (void)p;
-  return F.sensitive ? CUROB_PRECISION_EXACT : CUROB_PRECISION_TF32X3;
+  if (!F.sensitive) return CUROB_PRECISION_TF32X3;
+  const int all = (1 << F.ncomp) - 1;
+  return (F.composition && F.sens_mask != all) ? CUROB_PRECISION_MIXED : CUROB_PRECISION_EXACT;
 }
 
 namespace {
@@ -1196,6 +1232,10 @@ void mma_fill_args(void* dst, const MmaPlan& p, const Tables& tb, const Function
   a.onat = p.onat;
   a.nstage = g.nstage;
   a.stage_bytes = g.stage_bytes;
+  a.nlist = F.ncomp;
+  for (int i = 0; i < kMaxComponents; ++i) a.list[i] = i;
+  a.gout = nullptr;
+  a.d2out = nullptr;
   memcpy(dst, &a, sizeof(a));
 }
 
@@ -1212,6 +1252,30 @@ cudaError_t launch_mma_batch(const void* d_args, const int2* d_work, int nwork, 
 }
 
 int mma_max_block() { return kMaxNpad; }
+
+cudaError_t launch_mma_mixed(const MmaPlan& p, const Tables& tb, const Function& F,
+                             const float* x, int N, float* out, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  int ex[kMaxComponents], tf[kMaxComponents], nex = 0, ntf = 0;
+  for (int c = 0; c < F.ncomp; ++c) {
+    if (F.sens_mask >> c & 1) ex[nex++] = c;
+    else tf[ntf++] = c;
+  }
+  if (nex == 0) return launch_mode<M_TF32>(p, tb, F, x, N, out, st);
+  if (ntf == 0) return launch_mode<M_EXACT>(p, tb, F, x, N, out, st);
+  double* buf = nullptr;
+  const size_t n = (size_t)kMaxComponents * N;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), 2 * n * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  e = launch_mode<M_EXACT>(p, tb, F, x, N, out, st, ex, nex, buf, buf + n);
+  if (e == cudaSuccess) e = launch_mode<M_TF32>(p, tb, F, x, N, out, st, tf, ntf, buf, buf + n);
+  if (e == cudaSuccess) {
+    compose_kernel<<<(N + 255) / 256, 256, 0, st>>>(tb, F, buf, buf + n, N, out);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(buf, st);
+  return e;
+}
 
 cudaError_t launch_mma(const MmaPlan& p, const Tables& tb, const Function& F, int mode,
                        const float* x, int N, float* out, cudaStream_t st) {

@@ -28,8 +28,13 @@ curob_status mma_refresh(MmaPlan& p, const std::vector<Segment>& segs, const std
 void mma_release(MmaPlan& p);
 // True when every block of F fits the tensor-core kernel.
 bool mma_supports(const MmaPlan& p, const Function& F);
-// Precision AUTO picks for F (CUROB_PRECISION_TF32X3 or _EXACT).
+// Precision AUTO picks for F (CUROB_PRECISION_TF32X3, _EXACT or _MIXED).
 int mma_auto_mode(const MmaPlan& p, const Function& F);
+// AUTO for a composition whose members differ: the members with a kind that
+// magnifies contraction error on EXACT, the others on TF32X3, then their
+// composition (three launches on `st`).
+cudaError_t launch_mma_mixed(const MmaPlan& p, const Tables& tb, const Function& F,
+                             const float* x, int N, float* out, cudaStream_t st);
 // mode: CUROB_PRECISION_TF32X3, _BF16X3 or _EXACT.
 cudaError_t launch_mma(const MmaPlan& p, const Tables& tb, const Function& F, int mode,
                        const float* x, int N, float* out, cudaStream_t st);

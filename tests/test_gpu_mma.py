@@ -109,3 +109,28 @@ def test_ragged_tails(orc):
             got = gu.gpu_eval(fid, x32, torch.float32)
             ok, *_ = gu.fp32_check(orc, fid, D, 0, x32, got)
             assert ok, (N, fid)
+
+
+def test_mixed_compositions_choose_member_precisions():
+    """AUTO runs a composition whose members differ in sensitivity as MIXED:
+    members with Discus, Weierstrass, expanded Griewank-Rosenbrock or
+    Katsuura on EXACT, the others on TF32X3 (their parity is covered by the
+    AUTO sweeps above)."""
+    cu = gu.ensure(100, 256)
+    cu.curob_set_precision(cu.PRECISION_AUTO)
+    # CF4 (ID 32): Schwefel, HappyCat, Elliptic, Weierstrass, Griewank
+    assert cu.curob_query_precision(32) == cu.PRECISION_MIXED
+    assert [cu.curob_query_component_precision(32, c) for c in range(5)] == \
+        [cu.PRECISION_TF32X3] * 3 + [cu.PRECISION_EXACT, cu.PRECISION_TF32X3]
+    # a plain sensitive function and a plain insensitive one
+    assert cu.curob_query_precision(8) == cu.PRECISION_EXACT
+    assert cu.curob_query_precision(0) == cu.PRECISION_TF32X3
+    # forced modes stay whole-function
+    cu.curob_set_precision(cu.PRECISION_EXACT)
+    try:
+        assert cu.curob_query_precision(32) == cu.PRECISION_EXACT
+        assert cu.curob_query_component_precision(32, 0) == cu.PRECISION_EXACT
+    finally:
+        cu.curob_set_precision(cu.PRECISION_AUTO)
+    with pytest.raises(cu.CurobError):
+        cu.curob_set_precision(cu.PRECISION_MIXED)
