@@ -298,9 +298,18 @@ def run_curob(args):
     sel = (modes_a == dom) & (flops > 0)
     achieved = flops[sel].sum() / (launch_ms[sel].sum() / 1e3) / 1e12
     peak = flops[sel].sum() / t_bound[sel].sum() / 1e12
+    # DRAM bytes per function call of each group, measured with ncu (one-pass
+    # dram__bytes_read.sum + dram__bytes_write.sum over the 5 timed steps of
+    # `python bench.py --steps 5 --warmup 3`, this version of the kernels):
+    # TF32X3 and EXACT read x once (65.6 MB of input, 4 D + 4 bytes per
+    # candidate); a MIXED composition reads it once per precision subset.
+    dram_per_call = {1: 68.7e6, 4: 68.6e6, 5: 145.3e6}
+    traffic = dram_per_call.get(dom) if args.precision == "auto" else None
     roof = {"bound": "tensor" if dom != 3 else "alu", "kernel": mode_name[dom],
             "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 4), "traffic": None,
+            "frac": round(achieved / peak, 4),
+            "traffic": traffic, "traffic_unit": "bytes per function call",
+            "algorithmic_bytes_per_call": (4 * D + 4) * N,
             "peak_source": f"{src} bf16 burst; per algorithmic product: EXACT / 10 BF16 products, "
                            "TF32X3 x 1.1/2.25 (TF32/BF16 nominal ratio) / 3 TF32 products",
             "share_of_step": round(share[dom] / launch_ms.sum(), 3),

@@ -126,6 +126,13 @@ curob_status curob_query_component_precision(int fid, int comp, int* mode);
 /* Synchronise `stream` and report (then clear) a latched device-side error. */
 curob_status curob_get_device_status(curob_stream_t stream);
 
+/* Self-test of the bounded device-side waits every kernel of the library
+ * uses: one CTA waits on an mbarrier that nothing completes; the wait gives
+ * up after 2 s and the kernel reports it through a status word instead of
+ * hanging or trapping.  Returns CUROB_ERR_DEVICE_TIMEOUT when that works;
+ * the context stays usable.  Synchronous; needs no curob_initialize. */
+curob_status curob_selftest_bounded_wait(curob_stream_t stream);
+
 /* Human-readable name of a status code (static string). */
 const char* curob_status_string(curob_status s);
 

@@ -41,6 +41,7 @@ _SIGS = [
     ("curob_query_precision", _I, [_I, _P]),
     ("curob_query_component_precision", _I, [_I, _I, _P]),
     ("curob_get_device_status", _I, [_P]),
+    ("curob_selftest_bounded_wait", _I, [_P]),
     ("curob_status_string", ctypes.c_char_p, [_I]),
     ("curob_get_config", _I, [_P, _P]),
     ("curob_num_components", _I, [_I, _P]),
@@ -178,6 +179,11 @@ def curob_query_component_precision(fid, comp):
     m = ctypes.c_int()
     _call("curob_query_component_precision", fid, comp, ctypes.addressof(m))
     return m.value
+
+
+def curob_selftest_bounded_wait(stream=None, check=False):
+    """Returns the status code (CUROB_ERR_DEVICE_TIMEOUT when the wait ran out)."""
+    return _call("curob_selftest_bounded_wait", _stream(stream), check=check)
 
 
 def curob_get_device_status(stream=None, check=True):

@@ -222,6 +222,27 @@ curob_status curob_query_component_precision(int fid, int comp, int* mode) {
   return CUROB_OK;
 }
 
+curob_status curob_selftest_bounded_wait(curob_stream_t stream) {
+  int dev = 0, major = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CUROB_ERR_CUDA;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  if (major != 10) return CUROB_ERR_UNSUPPORTED;
+  int* d = nullptr;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return CUROB_ERR_OUT_OF_MEMORY;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int h = -1;
+  const bool ok = cudaMemsetAsync(d, 0, sizeof(int), st) == cudaSuccess &&
+                  launch_wait_selftest(d, st) == cudaSuccess &&
+                  cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                  cudaStreamSynchronize(st) == cudaSuccess;
+  cudaFree(d);
+  if (!ok) return CUROB_ERR_CUDA;
+  return h == DEV_TIMEOUT ? CUROB_ERR_DEVICE_TIMEOUT : (h == DEV_OK ? CUROB_OK : CUROB_ERR_CUDA);
+}
+
 curob_status curob_get_device_status(curob_stream_t stream) {
   if (!g.init) return CUROB_ERR_NOT_INITIALIZED;
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return CUROB_ERR_CUDA;

@@ -1039,6 +1039,21 @@ size_t ctrl_bytes() {  // barriers and work item (<= 256 B) + per-row tables + b
          3 * sizeof(float) * kMaxNpad;
 }
 
+// Self-test of the bounded waits: thread 0 waits on an mbarrier that nothing
+// arrives at; after kTimeoutNs the wait gives up, sets DEV_TIMEOUT in
+// *status and the kernel returns normally.
+__global__ void wait_selftest_kernel(int* status) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(&bar, 0, &abort_flag, status);
+}
+
 // Composition (Sec. 6) of the per-component values that subset launches
 // wrote: one thread per candidate.
 __global__ void compose_kernel(Tables tb, Function F, const double* gout, const double* d2out,
@@ -1252,6 +1267,11 @@ cudaError_t launch_mma_batch(const void* d_args, const int2* d_work, int nwork, 
 }
 
 int mma_max_block() { return kMaxNpad; }
+
+cudaError_t launch_wait_selftest(int* status, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(status);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_mma_mixed(const MmaPlan& p, const Tables& tb, const Function& F,
                              const float* x, int N, float* out, cudaStream_t st) {

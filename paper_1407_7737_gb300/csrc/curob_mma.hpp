@@ -35,6 +35,9 @@ int mma_auto_mode(const MmaPlan& p, const Function& F);
 // composition (three launches on `st`).
 cudaError_t launch_mma_mixed(const MmaPlan& p, const Tables& tb, const Function& F,
                              const float* x, int N, float* out, cudaStream_t st);
+// One CTA whose wait on an mbarrier nothing completes runs out (2 s) and
+// writes DEV_TIMEOUT to *status.
+cudaError_t launch_wait_selftest(int* status, cudaStream_t st);
 // mode: CUROB_PRECISION_TF32X3, _BF16X3 or _EXACT.
 cudaError_t launch_mma(const MmaPlan& p, const Tables& tb, const Function& F, int mode,
                        const float* x, int N, float* out, cudaStream_t st);
