@@ -98,30 +98,46 @@ def barrier(pg):
 # clocks sampled during the timed region
 # --------------------------------------------------------------------------
 class ClockSampler:
+    """nvidia-smi every 50 ms; each line is stamped on arrival and only the
+    lines stamped between mark_start() and mark_end() (plus one interval)
+    count, so the figures describe the timed region and not its set-up."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 50
 
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.proc = None
         self.lines = []
+        self.first = threading.Event()
+        self.t_start = self.t_end = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            self.first.wait(timeout=10.0)  # sampler running before the region opens
         except Exception:
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+            self.first.set()
+
+    def mark_start(self):
+        self.t_start = time.monotonic()
+
+    def mark_end(self):
+        self.t_end = time.monotonic()
+        # one more sample after the region closes, so short regions get one
+        time.sleep(1.5 * self.INTERVAL_MS / 1e3)
 
     def __exit__(self, *a):
         if self.proc:
@@ -134,7 +150,11 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lo = self.t_start if self.t_start is not None else float("-inf")
+        hi = (self.t_end + self.INTERVAL_MS / 1e3) if self.t_end is not None else float("inf")
+        for t, ln in self.lines:
+            if not lo <= t <= hi:
+                continue
             f = [v.strip() for v in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -149,7 +169,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "interval_ms": self.INTERVAL_MS}
 
 
 # --------------------------------------------------------------------------
@@ -212,11 +232,13 @@ def run_curob(args):
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        clk.mark_start()
         t0.record(stream)
         for s in range(args.steps):
             step(evs[s])
         t1.record(stream)
         torch.cuda.synchronize()
+        clk.mark_end()
     barrier(pg)
     cu.curob_get_device_status(stream)
     ms_total = t0.elapsed_time(t1)
