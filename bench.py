@@ -250,6 +250,7 @@ def run_curob(args):
     value = weak_throughput(NFUN * N, world, ms_step)
 
     modes = [cu.curob_query_precision(f) for f in range(NFUN)]
+    launches = [cu.curob_query_launches(f, N) for f in range(NFUN)]  # kernels per call
 
     def timed_pass(mode):
         """Step time (ms) of all 37 functions with the precision forced."""
@@ -301,9 +302,11 @@ def run_curob(args):
     bf16 = pk["bf16_tflops"]
     mode_peak = {1: bf16 * (1.1 / 2.25) / 3.0, 2: bf16 / 3.0, 4: bf16 / 10.0,
                  3: 152 * 128 * 2 * 2.07e9 / 1e12 / 6.0}
-    mode_name = {1: "mma_eval_kernel<TF32X3>", 2: "mma_eval_kernel<BF16X3>",
-                 4: "mma_eval_kernel<EXACT>", 3: "eval_simt_f32_kernel",
-                 5: "mma_eval_kernel<EXACT> + <TF32X3> (mixed compositions)"}
+    mode_name = {1: "mma_eval_kernel<TF32X3> (+ finish_kernel for heavy kinds)",
+                 2: "mma_eval_kernel<BF16X3> (+ finish_kernel for heavy kinds)",
+                 4: "mma_eval_kernel<EXACT> (+ finish_kernel for heavy kinds)",
+                 3: "eval_simt_f32_kernel",
+                 5: "mma_eval_kernel<EXACT> + <TF32X3> + finish_kernel (mixed compositions)"}
     flops = np.zeros(NFUN)
     t_bound = np.zeros(NFUN)  # seconds at the tensor peaks of the components' precisions
     for f in range(NFUN):
@@ -323,9 +326,11 @@ def run_curob(args):
     # DRAM bytes per function call of each group, measured with ncu (one-pass
     # dram__bytes_read.sum + dram__bytes_write.sum over the 5 timed steps of
     # `python bench.py --steps 5 --warmup 3`, this version of the kernels):
-    # TF32X3 and EXACT read x once (65.6 MB of input, 4 D + 4 bytes per
-    # candidate); a MIXED composition reads it once per precision subset.
-    dram_per_call = {1: 68.7e6, 4: 68.6e6, 5: 145.3e6}
+    # a light call reads x once (65.6 MB of input, 4 D + 4 bytes per
+    # candidate); a heavy-kind member adds its z round trip through the
+    # scratch (written by the tensor-core kernel, read by finish_kernel); a
+    # MIXED composition reads x once per precision subset.
+    dram_per_call = {1: 111.3e6, 4: 124.5e6, 5: 328.6e6}
     traffic = dram_per_call.get(dom) if args.precision == "auto" else None
     roof = {"bound": "tensor" if dom != 3 else "alu", "kernel": mode_name[dom],
             "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
@@ -335,7 +340,7 @@ def run_curob(args):
             "peak_source": f"{src} bf16 burst; per algorithmic product: EXACT / 10 BF16 products, "
                            "TF32X3 x 1.1/2.25 (TF32/BF16 nominal ratio) / 3 TF32 products",
             "share_of_step": round(share[dom] / launch_ms.sum(), 3),
-            "launches_per_step": int(sel.sum()),
+            "launches_per_step": int(np.array(launches)[sel].sum()),
             "note": "achieved = algorithmic flops (2*sum n_b^2 per candidate and rotated "
                     "component) / CUDA-event time of those functions' calls"}
     # per function: time against its tensor bound and the HBM bound of
@@ -376,7 +381,7 @@ def run_curob(args):
         surrogate = surrogate_bench(cu, torch, dev, stream, args)
         cu.curob_initialize(D, N, SEED)
 
-    gpu_launches = NFUN * args.steps
+    gpu_launches = int(sum(launches)) * args.steps
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": "evals/s", "n_gpus": world,
@@ -392,6 +397,7 @@ def run_curob(args):
             "per_function_ms": [round(v, 4) for v in launch_ms.tolist()],
             "per_function_path": [{1: "tf32x3", 2: "bf16x3", 3: "simt", 4: "exact",
                                    5: "mixed"}[m] for m in modes],
+            "per_function_launches": launches,
             "roofline": roof, "roofline_per_function": per_fn, "cpu_baseline": cpu, "e2e": e2e, "ragged_batch": ragged,
             "surrogate": surrogate, "clocks": clk.summary(), "gpu_launches": gpu_launches,
         }

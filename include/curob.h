@@ -118,6 +118,17 @@ curob_status curob_set_precision(int mode);
  * UNSUPPORTED (a forced tensor-core precision the instance cannot use). */
 curob_status curob_query_precision(int fid, int* mode);
 
+/* Number of kernel launches curob_evaluatef(fid, ., N, ., .) makes under the
+ * current precision: 1 for a function whose blocks are all evaluated in the
+ * tensor-core epilogue; one per precision group plus a finish kernel when a
+ * block has a heavy kind (Powers, Weierstrass, Griewank, Schaffer F7,
+ * expanded Griewank-Rosenbrock, Modified Schwefel, Katsuura, expanded
+ * Schaffer F6: their terms run in a separate kernel over z) or the function
+ * is a MIXED composition; times the number of candidate slices (scratch is
+ * bounded to 256 MB per slice).  Errors: as curob_query_precision, and
+ * INVALID_ARGUMENT for N < 0. */
+curob_status curob_query_launches(int fid, int N, int* launches);
+
 /* The precision component `comp` of fid runs at (the same as
  * curob_query_precision except for MIXED compositions, where it is EXACT or
  * TF32X3 per member).  INVALID_ARGUMENT for comp outside the function. */
@@ -175,8 +186,12 @@ curob_status curob_get_optimum(int fid, double* xopt);
  * work list, argument blocks and work counter live in a 160 KB static device
  * array that every GPU loading the library holds until the process exits.
  * fids[i], x[i] (device, N[i] x D), N[i], out[i] (device, N[i]) describe item
- * i; all host arrays.  Every item uses the EXACT contraction (same values as
- * curob_evaluatef with CUROB_PRECISION_EXACT).  Limits: at most 64 items and
+ * i; all host arrays.  Every item uses the EXACT contraction, and every kind
+ * is closed in the kernel's epilogue: the values of curob_evaluatef with
+ * CUROB_PRECISION_EXACT bit for bit where that call makes one launch
+ * (curob_query_launches); where it evaluates heavy kinds in a second kernel,
+ * the same within the FP32 tolerance (the partial sums round differently).
+ * Limits: at most 64 items and
  * 16384 tiles of 128 candidates per call (CUROB_ERR_CAPACITY beyond), each
  * N[i] <= max_concurrency, block widths <= 512 (else UNSUPPORTED).  The
  * first call on a device looks the array's address up.  All calls share the

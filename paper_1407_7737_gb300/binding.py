@@ -40,6 +40,7 @@ _SIGS = [
     ("curob_set_precision", _I, [_I]),
     ("curob_query_precision", _I, [_I, _P]),
     ("curob_query_component_precision", _I, [_I, _I, _P]),
+    ("curob_query_launches", _I, [_I, _I, _P]),
     ("curob_get_device_status", _I, [_P]),
     ("curob_selftest_bounded_wait", _I, [_P]),
     ("curob_status_string", ctypes.c_char_p, [_I]),
@@ -179,6 +180,12 @@ def curob_query_component_precision(fid, comp):
     m = ctypes.c_int()
     _call("curob_query_component_precision", fid, comp, ctypes.addressof(m))
     return m.value
+
+
+def curob_query_launches(fid, N):
+    n = ctypes.c_int()
+    _call("curob_query_launches", fid, N, ctypes.addressof(n))
+    return n.value
 
 
 def curob_selftest_bounded_wait(stream=None, check=False):

@@ -222,6 +222,18 @@ curob_status curob_query_component_precision(int fid, int comp, int* mode) {
   return CUROB_OK;
 }
 
+curob_status curob_query_launches(int fid, int N, int* launches) {
+  int m = 0;
+  curob_status rc = curob_query_precision(fid, &m);
+  if (rc != CUROB_OK) return rc;
+  if (!launches) return CUROB_ERR_NULL_POINTER;
+  if (N < 0) return CUROB_ERR_INVALID_ARGUMENT;
+  if (N == 0) *launches = 0;
+  else if (m == CUROB_PRECISION_SIMT) *launches = 1;
+  else *launches = mma_launch_count(g.inst.func[fid], m, N);
+  return CUROB_OK;
+}
+
 curob_status curob_selftest_bounded_wait(curob_stream_t stream) {
   int dev = 0, major = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return CUROB_ERR_CUDA;

@@ -225,8 +225,8 @@ curob_status curob_batch_run_separate(curob_batch b, curob_stream_t stream) {
     const curob_batch_item& it = b->items[i];
     if (it.N == 0) continue;
     Instance* I = b->item_inst[i];
-    if (launch_mma(I->mma, I->tables(), I->func[it.fid], CUROB_PRECISION_EXACT, it.x, it.N,
-                   it.out, (cudaStream_t)stream) != cudaSuccess)
+    if (launch_mma_fused(I->mma, I->tables(), I->func[it.fid], CUROB_PRECISION_EXACT, it.x,
+                         it.N, it.out, (cudaStream_t)stream) != cudaSuccess)
       return CUROB_ERR_CUDA;
   }
   return CUROB_OK;

@@ -45,6 +45,8 @@ struct Segment {
   long long tau_off;  // row scales of R_b's integer slices (tensor-core EXACT)
   int npad;           // n rounded up to the tensor-core tile
   int comp;           // owning component (index into the component table)
+  int hoff;           // heavy kinds: first column of the block among its function's
+                      // heavy columns (tensor-core z scratch); -1 otherwise
 };
 
 struct Component {
@@ -62,6 +64,7 @@ struct Function {
                       // expanded Griewank-Rosenbrock (cos of g2 ~ 1e4),
                       // Katsuura (2^j phases)
   int sens_mask;      // bit c: component c has such a kind
+  int hcols;          // variables of the function's heavy-kind blocks (kind_is_heavy)
 };
 
 // Device view of an initialised instance.
@@ -135,12 +138,19 @@ __host__ __device__ inline Acc<T> acc_zero() {
   return Acc<T>{T(0), T(0), T(0), T(1)};
 }
 
-__host__ __device__ inline bool kind_has_pairs(int k) {
+__host__ __device__ constexpr bool kind_has_pairs(int k) {
   return k == K_SCHAFFER7 || k == K_EGR || k == K_ROSENBROCK || k == K_SCHAFFER6;
 }
 __host__ __device__ inline bool kind_is_cyclic(int k) { return k == K_EGR || k == K_SCHAFFER6; }
 __host__ __device__ inline bool kind_is_sensitive(int k) {
   return k == K_DISCUS || k == K_WEIERSTRASS || k == K_EGR || k == K_KATSUURA;
+}
+// Kinds whose per-variable term calls transcendentals with slow paths (large
+// arguments, long series): many instructions per variable, so the
+// tensor-core path evaluates them with more threads than its epilogue has.
+__host__ __device__ constexpr bool kind_is_heavy(int k) {
+  return k == K_POWERS || k == K_WEIERSTRASS || k == K_GRIEWANK || k == K_SCHAFFER7 ||
+         k == K_EGR || k == K_SCHWEFEL || k == K_KATSUURA || k == K_SCHAFFER6;
 }
 
 // Math wrappers so one statement of each formula serves FP64 and FP32.

@@ -135,6 +135,7 @@ void Instance::build_tables() {
     F.max_n = 0;
     F.sensitive = 0;
     F.sens_mask = 0;
+    F.hcols = 0;
     for (int c = 0; c < ci.n; ++c) {
       const Member& m = ci.m[c];
       CompHost ch;
@@ -182,6 +183,11 @@ void Instance::build_tables() {
         s.img_off = -1;
         s.npad = 0;
         s.comp = (int)comps.size();
+        s.hoff = -1;
+        if (kind_is_heavy(s.kind)) {  // the blocks of a function stay consecutive
+          s.hoff = F.hcols;
+          F.hcols += s.n;
+        }
         F.max_n = std::max(F.max_n, s.n);
         if (kind_is_sensitive(s.kind)) {
           F.sensitive = 1;

@@ -26,19 +26,24 @@
 // they take EXACT.
 //
 // Warp roles of one CTA (one tile of 128 candidates, 1 CTA per SM):
-//   warps 0-3  producers: thread = candidate row.  Per block the block's
-//              index list and o hi/lo words are staged in shared memory; per
-//              K stage a thread gathers its row's x at the block's variables
-//              (prefetching the next stage's values), takes y = x - o in
-//              double-float (exact TwoSum, then o's low word), splits or
-//              slices it and stores its 64-byte rows of the A operand in the
-//              64-byte-swizzled K-major layout; it also sums ||x - o||^2.
-//   warps 4-7  epilogue: thread t owns row t (TMEM lane t), loads its z
-//              32 columns at a time (tcgen05.ld), applies z = s z + c, the
+//   warps 0-7  producers: warp w takes rows 32 (w % 4) .. + 31 (thread =
+//              candidate row) and half w / 4 of every K stage's columns.  Per
+//              block the block's index list and o hi/lo words are staged in
+//              shared memory; per stage a thread gathers its row's x at the
+//              block's variables (cp.async, issued stages ahead), takes
+//              y = x - o in double-float (exact TwoSum, then o's low word),
+//              splits or slices it and stores its rows of the A operand in the
+//              swizzled K-major layout; it also sums ||x - o||^2.
+//   warps 8-11 epilogue: thread t owns row t (TMEM lane t), loads its z 32
+//              columns at a time (tcgen05.ld), applies z = s z + c, the
 //              per-variable transform and the running sums (FP32 per 32
-//              columns, FP64 across), closes functions.
-//   warp 8     allocates TMEM and issues the MMAs (one lane).
-//   warp 9     loads the B operand (R_b parts, pre-laid-out in global memory
+//              columns, FP64 across), closes functions.  Blocks of a heavy
+//              kind (kind_is_heavy) instead leave z in a variable-major
+//              scratch, and finish_kernel, a second launch with 16 warps per
+//              32 candidates, evaluates their terms: four epilogue warps per
+//              SM cannot hide the latency of long transcendental series.
+//   warp 12    allocates TMEM and issues the MMAs (one lane).
+//   warp 13    loads the B operand (R_b parts, pre-laid-out in global memory
 //              as the exact shared-memory image) with one bulk copy per stage
 //              (cp.async.bulk, the TMA engine).
 // Stages rotate through shared memory under full/empty mbarriers; the
@@ -60,6 +65,10 @@ namespace {
 using namespace tc;
 
 constexpr int kTileM = 128;
+// Scratch of one slice of candidates: G_c and ||x - o_c||^2 (FP64) and the
+// heavy-kind z (FP32) of every row; slices keep it under this many bytes.
+constexpr size_t kScratchCap = size_t(256) << 20;
+
 constexpr int kThreads = 448;  // 8 producer, 4 epilogue, MMA and loader warps
 constexpr int kMmaWarp = 12, kLoaderWarp = 13;
 constexpr int kMaxNpad = 512;                    // TMEM columns
@@ -131,8 +140,10 @@ struct MmaArgs {
   int stage_bytes;
   int nlist;                   // components evaluated, in order (all of F's, or a subset)
   int list[kMaxComponents];
-  double* gout;                // subset launches: G_c and ||x - o_c||^2 per component and row
-  double* d2out;               // ([kMaxComponents][N] each), composed by compose_kernel
+  double* gout;                // split launches: G_c and ||x - o_c||^2 per component and row
+  double* d2out;               // ([kMaxComponents][N] each), closed by finish_kernel
+  float* zbuf;                 // heavy-kind z, variable-major ([F.hcols][N]); nullptr: the
+                               // epilogue evaluates heavy kinds itself
 };
 
 // Floats reserved per block for each precision's image (the TF32 size; BF16
@@ -160,15 +171,12 @@ struct EpiSeg {
   int gpos, gfirst;
 };
 
-// Kinds whose per-variable term calls transcendentals with slow paths (large
-// arguments): their terms are out-of-line calls on four variables at a time,
-// so the unrolled chunk loop stays small while the four independent
-// evaluations interleave (one epilogue warp per scheduler has no other warp
-// to hide their latency); contributions come back by value (no local memory).
-__host__ __device__ constexpr bool kind_is_heavy(int k) {
-  return k == K_POWERS || k == K_WEIERSTRASS || k == K_GRIEWANK || k == K_SCHAFFER7 ||
-         k == K_EGR || k == K_SCHWEFEL || k == K_KATSUURA || k == K_SCHAFFER6;
-}
+// Heavy kinds (kind_is_heavy) evaluated in the epilogue (persistent batch
+// kernel, or no z scratch): their terms are out-of-line calls on four
+// variables at a time, so the unrolled chunk loop stays small while the four
+// independent evaluations interleave (one epilogue warp per scheduler has no
+// other warp to hide their latency); contributions come back by value (no
+// local memory).
 // Sums (a0, a1, a2) and product (p) of the terms of the first n <= 4 of four
 // consecutive variables.
 template <int KIND>
@@ -379,7 +387,7 @@ __device__ inline void write_outputs(const MmaArgs& a, const Smem& m, long long 
   const long long grow = row0 + r;
   if (grow >= a.N) return;
   const Function& F = a.F;
-  if (a.gout) {  // a subset of the components: their values for compose_kernel
+  if (a.gout) {  // split launch: the components' values for finish_kernel
     for (int li = 0; li < a.nlist; ++li) {
       const int ci = a.list[li];
       a.gout[(size_t)ci * a.N + grow] = m.rowG[ci * kTileM + r];
@@ -692,7 +700,6 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
 template <int kMode>
 __device__ void epilogue_tile(const MmaArgs& a, const Smem& m, long long row0, RoleState& rs) {
   CUROB_ROLE_PROLOGUE
-  (void)row0;
     // ------------------------------------------------------------- epilogue
     const int q = warp - 8;                 // TMEM lane quadrant (warp % 4)
     const int r = q * 32 + lane;            // candidate row in the tile
@@ -723,6 +730,11 @@ __device__ void epilogue_tile(const MmaArgs& a, const Smem& m, long long row0, R
         es.gpos = sg.gpos;
         es.gfirst = sg.gfirst;
         const float* tau = a.tau + sg.tau_off;
+        // heavy kinds with a z scratch: the rows' z go out, variable-major
+        // (a warp's store of one variable covers 32 consecutive rows)
+        const bool zout = a.zbuf != nullptr && sg.hoff >= 0;
+        const long long grow = row0 + r;
+        float* zcol = zout ? a.zbuf + (size_t)sg.hoff * a.N + (grow < a.N ? grow : 0) : nullptr;
         if (sg.gfirst) st.open();
         const int nchunk = kMode == M_EXACT ? exact_nchunk(sg.npad) : 1;
         const int nw = kMode == M_EXACT ? exact_nw(sg.npad) : sg.npad;
@@ -748,13 +760,22 @@ __device__ void epilogue_tile(const MmaArgs& a, const Smem& m, long long row0, R
             } else {
               tmem_ld32(t_lane + (uint32_t)c, v);
             }
-            epi_chunk(kind, v, c, min(32, c_hi - c), es, st);
+            if (zout) {
+              if (grow < a.N) {
+                const int cend = min(32, c_hi - c);
+#pragma unroll
+                for (int k = 0; k < 32; ++k)
+                  if (k < cend) zcol[(size_t)(c + k) * a.N] = v[k] * es.s + es.c0;
+              }
+            } else {
+              epi_chunk(kind, v, c, min(32, c_hi - c), es, st);
+            }
           }
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(tmem_empty);
         }
-        if (ok && sg.glast) gsum += st.close(kind, sg.gn);
+        if (ok && sg.glast && !zout) gsum += st.close(kind, sg.gn);
       }
       if (!ok) break;
       rowG[ci * kTileM + r] = gsum;
@@ -1054,24 +1075,132 @@ __global__ void wait_selftest_kernel(int* status) {
   if (threadIdx.x == 0) mbar_wait(&bar, 0, &abort_flag, status);
 }
 
-// Composition (Sec. 6) of the per-component values that subset launches
-// wrote: one thread per candidate.
-__global__ void compose_kernel(Tables tb, Function F, const double* gout, const double* d2out,
-                               int N, float* out) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  double G[kMaxComponents], d2v[kMaxComponents];
-  for (int c = 0; c < F.ncomp; ++c) {
-    G[c] = gout[(size_t)c * N + i];
-    d2v[c] = d2out[(size_t)c * N + i];
+// ---------------------------------------------------------- finish kernel
+// Closes what split launches of the tensor-core kernel left: the basic
+// functions of heavy kind, from their z in the scratch (variable-major,
+// [F.hcols][N]); adds them to the component values G_c of the light kinds;
+// then composes (Sec. 6) or writes f.  A block takes 32 candidates
+// (threadIdx.x, so every load of one variable is one 128-byte line) and
+// kFinSlices slices of each block's variables (threadIdx.y); a slice sums its
+// terms in FP32 (at most 32 of them at D <= 512 per block), the slices are
+// added in FP64, as the epilogue adds its 32-column partial sums.
+constexpr int kFinSlices = 16;
+
+template <int KIND>
+__device__ __forceinline__ void fin_terms(const float* zc, long long ld, int j0, int j1, int gpos,
+                                          float gn, const float* aux, float kat_e,
+                                          Acc<float>& acc) {
+  if constexpr (kind_has_pairs(KIND)) {
+    // pairs (z_{g-1}, z_g) for function positions g = gpos + j >= 1; the
+    // function's blocks are consecutive in the scratch, so column j0 - 1 is
+    // the previous block's last variable when j0 = 0 < gpos
+    if (j0 >= j1) return;
+    float zp = (gpos + j0 > 0) ? zc[(long long)(j0 - 1) * ld] : 0.f;
+    for (int j = j0; j < j1; ++j) {
+      const float zj = zc[(long long)j * ld];
+      if (gpos + j > 0) acc.a0 += pair_term<float>(KIND, zp, zj);
+      zp = zj;
+    }
+  } else {
+#pragma unroll 4
+    for (int j = j0; j < j1; ++j) {
+      const float zj = zc[(long long)j * ld];
+      elem_term_f32(KIND, zj, zj, gpos + j, gn, aux ? aux[j] : 0.f, kat_e, acc);
+    }
   }
-  out[i] = (float)(compose(tb.comp + F.comp0, F.ncomp, G, d2v, tb.D) + kFopt);
+}
+
+__device__ __forceinline__ void fin_dispatch(int kind, const float* zc, long long ld, int j0,
+                                             int j1, int gpos, float gn, const float* aux,
+                                             float kat_e, Acc<float>& acc) {
+  switch (kind) {
+#define CUROB_FIN_CASE(K) \
+  case K: fin_terms<K>(zc, ld, j0, j1, gpos, gn, aux, kat_e, acc); break;
+    CUROB_FIN_CASE(K_POWERS) CUROB_FIN_CASE(K_WEIERSTRASS) CUROB_FIN_CASE(K_GRIEWANK)
+    CUROB_FIN_CASE(K_SCHAFFER7) CUROB_FIN_CASE(K_EGR) CUROB_FIN_CASE(K_SCHWEFEL)
+    CUROB_FIN_CASE(K_KATSUURA) CUROB_FIN_CASE(K_SCHAFFER6)
+#undef CUROB_FIN_CASE
+    default: break;
+  }
+}
+
+__global__ void __launch_bounds__(32 * kFinSlices, 2)
+finish_kernel(Tables tb, Function F, const float* zbuf, const double* gout, const double* d2out,
+              int N, float* out) {
+  __shared__ double red[4][kFinSlices][32];
+  __shared__ double Gs[kMaxComponents][32];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const long long i = (long long)blockIdx.x * 32 + tx;
+  const bool valid = i < N;
+  const long long ic = valid ? i : 0;  // rows past N read row 0 and write nothing
+  if (ty == 0)
+    for (int c = 0; c < F.ncomp; ++c) Gs[c][tx] = gout[(size_t)c * N + ic];
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, p = 1.0;
+  for (int c = 0; c < F.ncomp; ++c) {
+    const Component Cm = tb.comp[F.comp0 + c];
+    for (int si = 0; si < Cm.nseg; ++si) {
+      const Segment sg = tb.seg[Cm.seg0 + si];
+      if (sg.hoff < 0) continue;  // block-uniform: every thread takes the same path
+      if (sg.gfirst) {
+        a0 = a1 = a2 = 0.0;
+        p = 1.0;
+      }
+      const int L = (sg.n + kFinSlices - 1) / kFinSlices;
+      const int j0 = min(sg.n, ty * L), j1 = min(sg.n, j0 + L);
+      const float kat_e =
+          sg.kind == K_KATSUURA ? (float)(10.0 / pow((double)sg.gn, 1.2)) : 0.f;
+      const float* aux = sg.aux_off >= 0 ? tb.aux32 + sg.aux_off : nullptr;
+      const float* zc = zbuf + (size_t)sg.hoff * N + ic;
+      Acc<float> acc = acc_zero<float>();
+      fin_dispatch(sg.kind, zc, N, j0, j1, sg.gpos, (float)sg.gn, aux, kat_e, acc);
+      a0 += (double)acc.a0;
+      a1 += (double)acc.a1;
+      a2 += (double)acc.a2;
+      p *= (double)acc.p;
+      if (sg.glast) {
+        red[0][ty][tx] = a0;
+        red[1][ty][tx] = a1;
+        red[2][ty][tx] = a2;
+        red[3][ty][tx] = p;
+        __syncthreads();
+        if (ty == 0) {
+          double s0 = 0.0, s1 = 0.0, s2 = 0.0, pp = 1.0;
+          for (int t = 0; t < kFinSlices; ++t) {
+            s0 += red[0][t][tx];
+            s1 += red[1][t][tx];
+            s2 += red[2][t][tx];
+            pp *= red[3][t][tx];
+          }
+          if (kind_is_cyclic(sg.kind)) {  // (z_gn, z_1) closes the cycle
+            const float* zf = zbuf + (size_t)(sg.hoff - sg.gpos) * N + ic;
+            s0 += (double)pair_term<float>(sg.kind, zf[(size_t)(sg.gn - 1) * N], zf[0]);
+          }
+          Gs[c][tx] += finalize_f32(sg.kind, s0, s1, s2, pp, sg.gn);
+        }
+        __syncthreads();
+      }
+    }
+  }
+  if (ty != 0 || !valid) return;
+  double f;
+  if (F.composition) {
+    double G[kMaxComponents], d2v[kMaxComponents];
+    for (int c = 0; c < F.ncomp; ++c) {
+      G[c] = Gs[c][tx];
+      d2v[c] = d2out[(size_t)c * N + i];
+    }
+    f = compose(tb.comp + F.comp0, F.ncomp, G, d2v, tb.D);
+  } else {
+    f = Gs[0][tx];
+  }
+  out[i] = (float)(f + kFopt);
 }
 
 template <int kMode>
 cudaError_t launch_mode(const MmaPlan& p, const Tables& tb, const Function& F, const float* x,
                         int N, float* out, cudaStream_t st, const int* list = nullptr,
-                        int nlist = 0, double* gout = nullptr, double* d2out = nullptr) {
+                        int nlist = 0, double* gout = nullptr, double* d2out = nullptr,
+                        float* zbuf = nullptr) {
   const int npad_max = npad_of(F.max_n);
   const int ncmax = kMode == M_EXACT ? std::min(npad_max, kExactMaxNC) : npad_max;
   const size_t sb = stage_bytes_for<kMode>(ncmax);
@@ -1096,6 +1225,7 @@ cudaError_t launch_mode(const MmaPlan& p, const Tables& tb, const Function& F, c
   for (int i = 0; i < kMaxComponents; ++i) a.list[i] = list ? (i < nlist ? list[i] : 0) : i;
   a.gout = gout;
   a.d2out = d2out;
+  a.zbuf = zbuf;
   cudaError_t e = cudaFuncSetAttribute(mma_eval_kernel<kMode>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -1113,6 +1243,19 @@ curob_status mma_prepare(MmaPlan& p, std::vector<Segment>& segs, const Tables& t
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&cc_major, cudaDevAttrComputeCapabilityMajor, dev);
   p.ready = false;
+  {  // a private pool, so the split launches' scratch stays mapped between calls
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if (cudaMemPoolCreate(&p.pool, &props) == cudaSuccess) {
+      uint64_t keep = 2 * kScratchCap;
+      cudaMemPoolSetAttribute(p.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+      cudaGetLastError();
+      p.pool = nullptr;  // the device's default pool serves instead
+    }
+  }
   // per block: [TF32 | BF16 | EXACT] images and npad tau entries
   long long off = 0, toff = 0;
   for (Segment& s : segs) {
@@ -1190,6 +1333,8 @@ curob_status mma_refresh(MmaPlan& p, const std::vector<Segment>& segs, const std
 }
 
 void mma_release(MmaPlan& p) {
+  if (p.pool) cudaMemPoolDestroy(p.pool);  // freed once outstanding scratch is returned
+  p.pool = nullptr;
   cudaFree(p.img);
   cudaFree(p.ohi);
   cudaFree(p.olo);
@@ -1251,6 +1396,7 @@ void mma_fill_args(void* dst, const MmaPlan& p, const Tables& tb, const Function
   for (int i = 0; i < kMaxComponents; ++i) a.list[i] = i;
   a.gout = nullptr;
   a.d2out = nullptr;
+  a.zbuf = nullptr;
   memcpy(dst, &a, sizeof(a));
 }
 
@@ -1273,39 +1419,125 @@ cudaError_t launch_wait_selftest(int* status, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_mma_mixed(const MmaPlan& p, const Tables& tb, const Function& F,
-                             const float* x, int N, float* out, cudaStream_t st) {
-  if (N <= 0) return cudaSuccess;
-  int ex[kMaxComponents], tf[kMaxComponents], nex = 0, ntf = 0;
-  for (int c = 0; c < F.ncomp; ++c) {
-    if (F.sens_mask >> c & 1) ex[nex++] = c;
-    else tf[ntf++] = c;
+namespace {
+// One launch of the tensor-core kernel at precision `mode` over the
+// components `list` (all of F's when nullptr).
+cudaError_t launch_any(int mode, const MmaPlan& p, const Tables& tb, const Function& F,
+                       const float* x, int N, float* out, cudaStream_t st, const int* list,
+                       int nlist, double* gout, double* d2out, float* zbuf) {
+  switch (mode) {
+    case CUROB_PRECISION_TF32X3:
+      return launch_mode<M_TF32>(p, tb, F, x, N, out, st, list, nlist, gout, d2out, zbuf);
+    case CUROB_PRECISION_BF16X3:
+      return launch_mode<M_BF16>(p, tb, F, x, N, out, st, list, nlist, gout, d2out, zbuf);
+    case CUROB_PRECISION_EXACT:
+      return launch_mode<M_EXACT>(p, tb, F, x, N, out, st, list, nlist, gout, d2out, zbuf);
+    default: return cudaErrorInvalidValue;
   }
-  if (nex == 0) return launch_mode<M_TF32>(p, tb, F, x, N, out, st);
-  if (ntf == 0) return launch_mode<M_EXACT>(p, tb, F, x, N, out, st);
-  double* buf = nullptr;
-  const size_t n = (size_t)kMaxComponents * N;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), 2 * n * sizeof(double), st);
-  if (e != cudaSuccess) return e;
-  e = launch_mode<M_EXACT>(p, tb, F, x, N, out, st, ex, nex, buf, buf + n);
-  if (e == cudaSuccess) e = launch_mode<M_TF32>(p, tb, F, x, N, out, st, tf, ntf, buf, buf + n);
-  if (e == cudaSuccess) {
-    compose_kernel<<<(N + 255) / 256, 256, 0, st>>>(tb, F, buf, buf + n, N, out);
-    e = cudaGetLastError();
+}
+
+struct SplitPlan {
+  int ngroups = 0, mode[2] = {-1, -1}, list[2][kMaxComponents], nlist[2] = {0, 0};
+  bool direct = false;     // one launch straight to f: no scratch, no finish kernel
+  long long rows = 0;      // candidates per slice
+  size_t per_row = 0;      // scratch bytes per candidate
+};
+
+// Groups F's components by precision (cmode[c]) in component order.
+SplitPlan split_plan(const Function& F, const int* cmode, int N) {
+  SplitPlan sp;
+  for (int c = 0; c < F.ncomp; ++c) {
+    const int g = (sp.ngroups == 0 || sp.mode[0] == cmode[c]) ? 0 : 1;
+    if (g + 1 > sp.ngroups) sp.ngroups = g + 1;
+    sp.mode[g] = cmode[c];
+    sp.list[g][sp.nlist[g]++] = c;
+  }
+  sp.direct = sp.ngroups == 1 && F.hcols == 0;
+  sp.per_row = sizeof(float) * (size_t)F.hcols + 2 * sizeof(double) * kMaxComponents;
+  long long rows = (long long)(kScratchCap / sp.per_row) / kTileM * kTileM;
+  sp.rows = std::min<long long>(std::max<long long>(rows, kTileM), std::max(N, 1));
+  return sp;
+}
+
+// Evaluates F with component c at precision cmode[c] (at most two distinct
+// precisions).  Unless one launch can write f itself, every group writes its
+// components' G_c, ||x - o_c||^2 and heavy-kind z into a stream-ordered
+// scratch and finish_kernel closes the heavy kinds and composes.
+cudaError_t launch_split(const MmaPlan& p, const Tables& tb, const Function& F, const int* cmode,
+                         const float* x, int N, float* out, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  const SplitPlan sp = split_plan(F, cmode, N);
+  if (sp.direct)
+    return launch_any(sp.mode[0], p, tb, F, x, N, out, st, nullptr, 0, nullptr, nullptr, nullptr);
+  void* buf = nullptr;
+  const size_t bytes = sp.per_row * (size_t)sp.rows;
+  cudaError_t e = p.pool ? cudaMallocFromPoolAsync(&buf, bytes, p.pool, st)
+                         : cudaMallocAsync(&buf, bytes, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (sp.ngroups == 1)  // no room: the epilogue evaluates the heavy kinds itself
+      return launch_any(sp.mode[0], p, tb, F, x, N, out, st, nullptr, 0, nullptr, nullptr,
+                        nullptr);
+    return e;
+  }
+  for (long long r0 = 0; r0 < N && e == cudaSuccess; r0 += sp.rows) {
+    const int n = (int)std::min<long long>(sp.rows, N - r0);
+    double* g = static_cast<double*>(buf);
+    double* d2 = g + (size_t)kMaxComponents * n;
+    float* z = F.hcols > 0 ? reinterpret_cast<float*>(d2 + (size_t)kMaxComponents * n) : nullptr;
+    const float* xs = x + (size_t)r0 * tb.D;
+    for (int gi = 0; gi < sp.ngroups && e == cudaSuccess; ++gi)
+      e = launch_any(sp.mode[gi], p, tb, F, xs, n, out + r0, st, sp.list[gi], sp.nlist[gi], g,
+                     d2, z);
+    if (e == cudaSuccess) {
+      finish_kernel<<<(unsigned)((n + 31) / 32), dim3(32, kFinSlices), 0, st>>>(tb, F, z, g, d2,
+                                                                               n, out + r0);
+      e = cudaGetLastError();
+    }
   }
   cudaFreeAsync(buf, st);
   return e;
 }
 
+void component_modes(const Function& F, int mode, int* cmode) {
+  for (int c = 0; c < F.ncomp; ++c)
+    cmode[c] = mode != CUROB_PRECISION_MIXED
+                   ? mode
+                   : ((F.sens_mask >> c & 1) ? CUROB_PRECISION_EXACT : CUROB_PRECISION_TF32X3);
+}
+}  // namespace
+
+int mma_launch_count(const Function& F, int mode, int N) {
+  if (N <= 0) return 0;
+  int cmode[kMaxComponents];
+  component_modes(F, mode, cmode);
+  const SplitPlan sp = split_plan(F, cmode, N);
+  if (sp.direct) return 1;
+  const long long slices = (N + sp.rows - 1) / sp.rows;
+  return (int)(slices * (sp.ngroups + 1));
+}
+
+cudaError_t launch_mma_fused(const MmaPlan& p, const Tables& tb, const Function& F, int mode,
+                             const float* x, int N, float* out, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  return launch_any(mode, p, tb, F, x, N, out, st, nullptr, 0, nullptr, nullptr, nullptr);
+}
+
+cudaError_t launch_mma_mixed(const MmaPlan& p, const Tables& tb, const Function& F,
+                             const float* x, int N, float* out, cudaStream_t st) {
+  int cmode[kMaxComponents];
+  component_modes(F, CUROB_PRECISION_MIXED, cmode);
+  return launch_split(p, tb, F, cmode, x, N, out, st);
+}
+
 cudaError_t launch_mma(const MmaPlan& p, const Tables& tb, const Function& F, int mode,
                        const float* x, int N, float* out, cudaStream_t st) {
-  if (N <= 0) return cudaSuccess;
-  switch (mode) {
-    case CUROB_PRECISION_TF32X3: return launch_mode<M_TF32>(p, tb, F, x, N, out, st);
-    case CUROB_PRECISION_BF16X3: return launch_mode<M_BF16>(p, tb, F, x, N, out, st);
-    case CUROB_PRECISION_EXACT: return launch_mode<M_EXACT>(p, tb, F, x, N, out, st);
-    default: return cudaErrorInvalidValue;
-  }
+  if (mode != CUROB_PRECISION_TF32X3 && mode != CUROB_PRECISION_BF16X3 &&
+      mode != CUROB_PRECISION_EXACT)
+    return cudaErrorInvalidValue;
+  int cmode[kMaxComponents];
+  component_modes(F, mode, cmode);
+  return launch_split(p, tb, F, cmode, x, N, out, st);
 }
 
 }  // namespace curob

@@ -18,6 +18,7 @@ struct MmaPlan {
   float* onat = nullptr;     // o per component in natural order, FP32
   bool sm103 = false;        // the device runs tcgen05
   bool ready = false;
+  cudaMemPool_t pool = nullptr;  // stream-ordered scratch of split launches (kept warm)
 };
 
 // Lays out and fills the operand images (sets Segment::img_off / npad).
@@ -31,16 +32,26 @@ bool mma_supports(const MmaPlan& p, const Function& F);
 // Precision AUTO picks for F (CUROB_PRECISION_TF32X3, _EXACT or _MIXED).
 int mma_auto_mode(const MmaPlan& p, const Function& F);
 // AUTO for a composition whose members differ: the members with a kind that
-// magnifies contraction error on EXACT, the others on TF32X3, then their
-// composition (three launches on `st`).
+// magnifies contraction error on EXACT, the others on TF32X3, then the
+// finish kernel (heavy kinds, composition): three launches on `st`.
 cudaError_t launch_mma_mixed(const MmaPlan& p, const Tables& tb, const Function& F,
                              const float* x, int N, float* out, cudaStream_t st);
 // One CTA whose wait on an mbarrier nothing completes runs out (2 s) and
 // writes DEV_TIMEOUT to *status.
 cudaError_t launch_wait_selftest(int* status, cudaStream_t st);
-// mode: CUROB_PRECISION_TF32X3, _BF16X3 or _EXACT.
+// mode: CUROB_PRECISION_TF32X3, _BF16X3 or _EXACT.  A function with
+// heavy-kind blocks (kind_is_heavy) takes a second launch (finish kernel).
 cudaError_t launch_mma(const MmaPlan& p, const Tables& tb, const Function& F, int mode,
                        const float* x, int N, float* out, cudaStream_t st);
+
+// One launch of the tensor-core kernel over all of F's components, every
+// kind closed in its epilogue (the tile arithmetic of the persistent batch
+// kernel, launch by launch).
+cudaError_t launch_mma_fused(const MmaPlan& p, const Tables& tb, const Function& F, int mode,
+                             const float* x, int N, float* out, cudaStream_t st);
+// Kernel launches launch_mma / launch_mma_mixed make for F at N candidates
+// (mode CUROB_PRECISION_MIXED for the latter).
+int mma_launch_count(const Function& F, int mode, int N);
 
 // Persistent EXACT-mode launches over a ragged batch.
 size_t mma_args_bytes();

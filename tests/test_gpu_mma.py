@@ -134,3 +134,47 @@ def test_mixed_compositions_choose_member_precisions():
         cu.curob_set_precision(cu.PRECISION_AUTO)
     with pytest.raises(cu.CurobError):
         cu.curob_set_precision(cu.PRECISION_MIXED)
+
+
+def test_launch_counts_follow_the_split():
+    """One launch for a function whose blocks the epilogue closes; one per
+    precision group plus the finish kernel when a block has a heavy kind or
+    a composition mixes precisions."""
+    cu = gu.ensure(100, 256)
+    cu.curob_set_precision(cu.PRECISION_AUTO)
+    assert cu.curob_query_launches(0, 256) == 1    # Sphere, TF32X3
+    assert cu.curob_query_launches(3, 256) == 1    # Discus, EXACT, light
+    assert cu.curob_query_launches(8, 256) == 2    # Weierstrass: heavy
+    assert cu.curob_query_launches(16, 256) == 2   # rotated Modified Schwefel
+    assert cu.curob_query_launches(29, 256) == 3   # CF1: MIXED, no heavy member
+    assert cu.curob_query_launches(32, 256) == 3   # CF4: MIXED with heavy members
+    assert cu.curob_query_launches(8, 0) == 0
+    cu.curob_set_precision(3)  # SIMT: one kernel whatever the kinds
+    try:
+        assert cu.curob_query_launches(32, 256) == 1
+    finally:
+        cu.curob_set_precision(cu.PRECISION_AUTO)
+    with pytest.raises(cu.CurobError):
+        cu.curob_query_launches(8, -1)
+
+
+def test_heavy_scratch_slices(orc):
+    """A call whose heavy-kind scratch exceeds one slice (CF4 at D = 1000:
+    3000 heavy columns per candidate) runs in two candidate slices; rows on
+    both sides of the slice boundary match the oracle."""
+    import torch
+    D = 1000
+    per_row = 4 * 3000 + 2 * 8 * 5
+    rows_per_slice = (256 * 2**20 // per_row) // 128 * 128
+    N = rows_per_slice + 300
+    cu = gu.ensure(D, N)
+    cu.curob_set_precision(cu.PRECISION_AUTO)
+    assert cu.curob_query_launches(32, N) == 6
+    assert cu.curob_query_launches(32, rows_per_slice) == 3
+    o = orc.generate(32, D, 0)[0].o
+    x32 = inputs.mixed(N, D, 4242, center=o, frac_near=0.1, sigma=1e-3).astype(np.float32)
+    got = gu.gpu_eval(32, x32, torch.float32)
+    rows = np.unique(np.r_[0, 127, rows_per_slice - 1, rows_per_slice, rows_per_slice + 1, N - 1,
+                           np.random.default_rng(5).integers(0, N, 26)])
+    ok, worst, excused, raw = gu.fp32_check(orc, 32, D, 0, x32, got, rows)
+    assert ok, (worst, raw)

@@ -61,12 +61,19 @@ def test_noalloc_matches_evaluatef_twice(orc, torch_cuda):
         cu.curob_get_device_status(None)
         auto = _reference(cu, torch, fids, xs, cu.PRECISION_AUTO)
         exact = _reference(cu, torch, fids, xs, cu.PRECISION_EXACT)
-        for fid, o, a, e in zip(fids, outs, auto, exact):
+        cu.curob_set_precision(cu.PRECISION_EXACT)
+        fused = [cu.curob_query_launches(fid, n) == 1 for fid, n in zip(fids, Ns)]
+        cu.curob_set_precision(cu.PRECISION_AUTO)
+        assert not all(fused) and any(fused)  # both kinds of item are covered
+        for fid, o, a, e, one in zip(fids, outs, auto, exact, fused):
             got = o.cpu().numpy().astype(np.float64)
-            ref = a.cpu().numpy().astype(np.float64)
-            ok, tol = gu.fp32_ok(got, ref, gu.f_scale(orc, fid, D, 0))
-            assert ok.all(), (k, fid, float((np.abs(got - ref) / tol).max()))
-            assert torch.equal(o, e), (k, fid)  # same tile arithmetic as EXACT
+            fs = gu.f_scale(orc, fid, D, 0)
+            for ref_t in (a, e):
+                ref = ref_t.cpu().numpy().astype(np.float64)
+                ok, tol = gu.fp32_ok(got, ref, fs)
+                assert ok.all(), (k, fid, float((np.abs(got - ref) / tol).max()))
+            if one:  # EXACT in one launch: the same tile arithmetic, bit for bit
+                assert torch.equal(o, e), (k, fid)
 
 
 def test_noalloc_limits(torch_cuda):
