@@ -47,6 +47,7 @@ struct Segment {
   int comp;           // owning component (index into the component table)
   int hoff;           // heavy kinds: first column of the block among its function's
                       // heavy columns (tensor-core z scratch); -1 otherwise
+  float kat_e;        // Katsuura: the exponent 10 / gn^1.2 (FP32 paths); 0 otherwise
 };
 
 struct Component {
@@ -233,16 +234,23 @@ __device__ inline double weierstrass_inner(double z) {
 }
 // FP32: the phase frac(3^k (z + 1/2)) is carried exactly as a 40-bit binary
 // fraction (z is exact in it for |z| >= 2^-17), multiplied by 3 modulo 1 in
-// integer arithmetic, so rounding adds no phase error however large 3^k is;
-// cos(2 pi t) = -cos(2 pi (t - 1/2)) with the argument in [-pi, pi).
+// integer arithmetic, so rounding adds no phase error however large 3^k is.
+// Each term rounds the phase to 23 bits (error <= 2^-24 of a turn), which is
+// the mantissa of a float in [2^23, 2^24): OR-ing it into 2^23 and
+// subtracting 2^23 gives it exactly without an integer-to-float conversion;
+// cos(2 pi t) = -cos(2 pi (t - 1/2)) with the argument in [-pi, pi].
 __device__ inline float weierstrass_inner(float z) {
   const long long Z = __float2ll_rn(z * 1099511627776.0f);          // z 2^40
   unsigned long long P = (unsigned long long)(Z + 549755813888LL);   // (z + 1/2) 2^40
   float s = 0.f, ak = 1.f;
 #pragma unroll
   for (int k = 0; k <= 20; ++k) {
-    const float t = (float)((unsigned)(P >> 16) & 0xFFFFFFu) * 5.9604644775390625e-8f;
-    s = fmaf(-ak, __cosf(6.28318530717958647692f * (t - 0.5f)), s);
+    // bits 16..39 of P (the fraction's top 24), rounded to 23 (a carry out
+    // of the field wraps to 0: the same point of the circle)
+    const unsigned b = ((((unsigned)(P >> 16)) + 1u) >> 1) & 0x7FFFFFu;
+    const float t = __uint_as_float(0x4B000000u | b) - 8388608.0f;   // b, exactly
+    // 2 pi 2^-23 t - pi, one rounding
+    s = fmaf(-ak, __cosf(fmaf(t, 7.490140565847157e-07f, -3.14159265358979323846f)), s);
     ak *= 0.5f;
     P *= 3ull;  // the low 40 bits hold frac(3^{k+1} (z + 1/2))
   }
@@ -273,6 +281,26 @@ __device__ inline T katsuura_inner(T z) {
     itj = itj * T(0.5);
     T v = tj * z;
     s += m_fabs(v - m_rint(v)) * itj;
+  }
+  return s;
+}
+// FP32: the same terms from the signed fractional part f_j = 2^j z -
+// rint(2^j z), carried as f_j = w - rint(w), w = 2 f_{j-1} (2^j z differs
+// from w by an even integer): |w| <= 1, so w, its rounding (the 1.5 * 2^23
+// addition rounds to the nearest integer, ties to even as rint) and w -
+// rint(w) are all exact, and every term equals the direct one, without a
+// round-to-integer instruction per term.
+__device__ inline float katsuura_inner(float z) {
+  constexpr float kRnd = 12582912.0f;  // 1.5 * 2^23
+  float f = z - rintf(z);
+  float s = 0.f, itj = 1.f;
+#pragma unroll 8
+  for (int j = 1; j <= 32; ++j) {
+    const float w = f + f;
+    const float r = (w + kRnd) - kRnd;
+    f = w - r;
+    itj = itj * 0.5f;
+    s += fabsf(f) * itj;
   }
   return s;
 }

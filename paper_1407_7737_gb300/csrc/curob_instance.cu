@@ -3,6 +3,7 @@
 // component/block layout, the generated shifts, permutations and rotations,
 // and the tensor-core operand images.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -183,6 +184,7 @@ void Instance::build_tables() {
         s.img_off = -1;
         s.npad = 0;
         s.comp = (int)comps.size();
+        s.kat_e = s.kind == K_KATSUURA ? (float)(10.0 / std::pow((double)s.gn, 1.2)) : 0.f;
         s.hoff = -1;
         if (kind_is_heavy(s.kind)) {  // the blocks of a function stay consecutive
           s.hoff = F.hcols;

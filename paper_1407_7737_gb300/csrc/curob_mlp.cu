@@ -408,34 +408,44 @@ __global__ void mlp_prep_kernel(const float* __restrict__ x, int n, const float*
 }
 
 // Mean and standard deviation of t = log(max(f - f_opt, 0) + 1) over n
-// values, in FP64, one block, fixed summation order.
-__global__ void mlp_stats_kernel(const float* __restrict__ f, long long n, double f_opt,
-                                 double* out) {
-  __shared__ double sh[1024];
+// values, in FP64, in a fixed summation order: a fixed grid of kStatBlocks
+// blocks writes one partial sum each (thread-strided sums, then a tree), and
+// one block adds the partials in block order.  Pass 0 sums t, pass 1 sums
+// (t - mu)^2 with mu from pass 0.
+constexpr int kStatBlocks = 256, kStatThreads = 256;
+
+__global__ void __launch_bounds__(kStatThreads) mlp_stats_partial_kernel(
+    const float* __restrict__ f, long long n, double f_opt, const double* __restrict__ stats,
+    int pass, double* __restrict__ partial) {
+  __shared__ double sh[kStatThreads];
+  const double mu = pass ? stats[0] : 0.0;
   double s = 0.0;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) s += log1p(fmax((double)f[i] - f_opt, 0.0));
+  for (long long i = (long long)blockIdx.x * kStatThreads + threadIdx.x; i < n;
+       i += (long long)kStatBlocks * kStatThreads) {
+    const double t = log1p(fmax((double)f[i] - f_opt, 0.0));
+    s += pass ? (t - mu) * (t - mu) : t;
+  }
   sh[threadIdx.x] = s;
   __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+  for (int w = kStatThreads / 2; w > 0; w >>= 1) {
     if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
     __syncthreads();
   }
-  const double mu = sh[0] / (double)n;
+  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(kStatBlocks) mlp_stats_final_kernel(
+    const double* __restrict__ partial, long long n, int pass, double* __restrict__ stats) {
+  __shared__ double sh[kStatBlocks];
+  sh[threadIdx.x] = partial[threadIdx.x];
   __syncthreads();
-  s = 0.0;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-    const double d = log1p(fmax((double)f[i] - f_opt, 0.0)) - mu;
-    s += d * d;
-  }
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+  for (int w = kStatBlocks / 2; w > 0; w >>= 1) {
     if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    out[0] = mu;
-    out[1] = sqrt(sh[0] / (double)n);
+    if (pass == 0) stats[0] = sh[0] / (double)n;
+    else stats[1] = sqrt(sh[0] / (double)n);
   }
 }
 
@@ -1003,7 +1013,7 @@ curob_status curob_surrogate_create(int max_batch, uint64_t seed, curob_surrogat
             dalloc(&s->G1D, B * kSurH) && dalloc(&s->T, B) &&
             dalloc(&s->pW1, tiles * kSurH * kSurInPad) && dalloc(&s->pW2, tiles * kSurH * kSurH) &&
             dalloc(&s->pb1, tiles * kSurH) && dalloc(&s->pv2, tiles * 2 * kSurH) &&
-            dalloc(&s->ps2, tiles * 2) && dalloc(&s->stats, 2) && dalloc(&s->d_status, 1) &&
+            dalloc(&s->ps2, tiles * 2) && dalloc(&s->stats, 2 + kStatBlocks) && dalloc(&s->d_status, 1) &&
             dalloc(&s->Uc, (size_t)s->chunk * kSurInPad) && dalloc(&s->H1c, (size_t)s->chunk * kSurH) &&
             ensure_select_scratch(s, 1 << 20) == CUROB_OK;
   ok = ok && cudaMemset(s->W1b, 0, sizeof(__nv_bfloat16) * kSurH * kSurInPad) == cudaSuccess &&
@@ -1123,7 +1133,14 @@ curob_status curob_surrogate_standardise(curob_surrogate s, const float* f, long
   std::lock_guard<std::mutex> lk(s->mtx);
   cudaStream_t st = (cudaStream_t)stream;
   double h[2];
-  mlp_stats_kernel<<<1, 1024, 0, st>>>(f, n, (double)f_opt, s->stats);
+  for (int pass = 0; pass < 2; ++pass) {
+    mlp_stats_partial_kernel<<<kStatBlocks, kStatThreads, 0, st>>>(f, n, (double)f_opt,
+                                                                    s->stats, pass,
+                                                                    s->stats + 2);
+    mlp_stats_final_kernel<<<1, kStatBlocks, 0, st>>>(s->stats + 2, n, pass, s->stats);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail("standardise", e);
   if (cudaMemcpyAsync(h, s->stats, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return CUROB_ERR_CUDA;

@@ -39,8 +39,8 @@
 //              per-variable transform and the running sums (FP32 per 32
 //              columns, FP64 across), closes functions.  Blocks of a heavy
 //              kind (kind_is_heavy) instead leave z in a variable-major
-//              scratch, and finish_kernel, a second launch with 16 warps per
-//              32 candidates, evaluates their terms: four epilogue warps per
+//              scratch, and finish_kernel, a second launch with 8 warps per
+//              16 candidates, evaluates their terms: four epilogue warps per
 //              SM cannot hide the latency of long transcendental series.
 //   warp 12    allocates TMEM and issues the MMAs (one lane).
 //   warp 13    loads the B operand (R_b parts, pre-laid-out in global memory
@@ -725,7 +725,7 @@ __device__ void epilogue_tile(const MmaArgs& a, const Smem& m, long long row0, R
         es.s = (float)sg.scale;
         es.c0 = (float)sg.offset;
         es.gnT = (float)sg.gn;
-        es.kat_e = (kind == K_KATSUURA) ? (float)(10.0 / pow((double)sg.gn, 1.2)) : 0.f;
+        es.kat_e = sg.kat_e;
         es.aux = sg.aux_off >= 0 ? tb.aux32 + sg.aux_off : nullptr;
         es.gpos = sg.gpos;
         es.gfirst = sg.gfirst;
@@ -1079,11 +1079,15 @@ __global__ void wait_selftest_kernel(int* status) {
 // Closes what split launches of the tensor-core kernel left: the basic
 // functions of heavy kind, from their z in the scratch (variable-major,
 // [F.hcols][N]); adds them to the component values G_c of the light kinds;
-// then composes (Sec. 6) or writes f.  A block takes 32 candidates
-// (threadIdx.x, so every load of one variable is one 128-byte line) and
+// then composes (Sec. 6) or writes f.  A block takes kFinX candidates
+// (threadIdx.x: every load of one variable is two full 32-byte sectors) and
 // kFinSlices slices of each block's variables (threadIdx.y); a slice sums its
-// terms in FP32 (at most 32 of them at D <= 512 per block), the slices are
-// added in FP64, as the epilogue adds its 32-column partial sums.
+// terms in FP32 (at most 32 at block widths <= 512), the slices are added in
+// FP64 (shuffles within a warp, then across the warps), as the epilogue adds
+// its 32-column partial sums.  The terms are latency-bound chains of
+// transcendentals: 8 blocks of 8 warps per SM (32 registers, a few spilled
+// to L1) beat fewer warps with no spills.
+constexpr int kFinX = 16;
 constexpr int kFinSlices = 16;
 
 template <int KIND>
@@ -1124,13 +1128,27 @@ __device__ __forceinline__ void fin_dispatch(int kind, const float* zc, long lon
   }
 }
 
-__global__ void __launch_bounds__(32 * kFinSlices, 2)
+__device__ __forceinline__ void fin_warp_sum(double& a0, double& a1, double& a2, double& p) {
+  // lanes tx, tx + kFinX, ... of a warp hold the same candidate
+#pragma unroll
+  for (int off = kFinX; off < 32; off <<= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, off);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, off);
+    p *= __shfl_xor_sync(0xffffffffu, p, off);
+  }
+}
+
+__global__ void __launch_bounds__(kFinX * kFinSlices, 8)
 finish_kernel(Tables tb, Function F, const float* zbuf, const double* gout, const double* d2out,
               int N, float* out) {
-  __shared__ double red[4][kFinSlices][32];
-  __shared__ double Gs[kMaxComponents][32];
+  constexpr int kWarps = kFinX * kFinSlices / 32;
+  constexpr int kSlicesPerWarp = 32 / kFinX;
+  __shared__ double red[4][kWarps][kFinX];
+  __shared__ double Gs[kMaxComponents][kFinX];
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const long long i = (long long)blockIdx.x * 32 + tx;
+  const int warp = ty / kSlicesPerWarp;
+  const long long i = (long long)blockIdx.x * kFinX + tx;
   const bool valid = i < N;
   const long long ic = valid ? i : 0;  // rows past N read row 0 and write nothing
   if (ty == 0)
@@ -1147,35 +1165,40 @@ finish_kernel(Tables tb, Function F, const float* zbuf, const double* gout, cons
       }
       const int L = (sg.n + kFinSlices - 1) / kFinSlices;
       const int j0 = min(sg.n, ty * L), j1 = min(sg.n, j0 + L);
-      const float kat_e =
-          sg.kind == K_KATSUURA ? (float)(10.0 / pow((double)sg.gn, 1.2)) : 0.f;
       const float* aux = sg.aux_off >= 0 ? tb.aux32 + sg.aux_off : nullptr;
       const float* zc = zbuf + (size_t)sg.hoff * N + ic;
       Acc<float> acc = acc_zero<float>();
-      fin_dispatch(sg.kind, zc, N, j0, j1, sg.gpos, (float)sg.gn, aux, kat_e, acc);
+      fin_dispatch(sg.kind, zc, N, j0, j1, sg.gpos, (float)sg.gn, aux, sg.kat_e, acc);
       a0 += (double)acc.a0;
       a1 += (double)acc.a1;
       a2 += (double)acc.a2;
       p *= (double)acc.p;
       if (sg.glast) {
-        red[0][ty][tx] = a0;
-        red[1][ty][tx] = a1;
-        red[2][ty][tx] = a2;
-        red[3][ty][tx] = p;
+        fin_warp_sum(a0, a1, a2, p);
+        if (ty % kSlicesPerWarp == 0) {
+          red[0][warp][tx] = a0;
+          red[1][warp][tx] = a1;
+          red[2][warp][tx] = a2;
+          red[3][warp][tx] = p;
+        }
         __syncthreads();
-        if (ty == 0) {
+        if (warp == 0) {  // lane (tx, q): warps q, q + 4, ...; then across q
+          const int q = ty % kSlicesPerWarp;
           double s0 = 0.0, s1 = 0.0, s2 = 0.0, pp = 1.0;
-          for (int t = 0; t < kFinSlices; ++t) {
-            s0 += red[0][t][tx];
-            s1 += red[1][t][tx];
-            s2 += red[2][t][tx];
-            pp *= red[3][t][tx];
+          for (int w = q; w < kWarps; w += kSlicesPerWarp) {
+            s0 += red[0][w][tx];
+            s1 += red[1][w][tx];
+            s2 += red[2][w][tx];
+            pp *= red[3][w][tx];
           }
-          if (kind_is_cyclic(sg.kind)) {  // (z_gn, z_1) closes the cycle
-            const float* zf = zbuf + (size_t)(sg.hoff - sg.gpos) * N + ic;
-            s0 += (double)pair_term<float>(sg.kind, zf[(size_t)(sg.gn - 1) * N], zf[0]);
+          fin_warp_sum(s0, s1, s2, pp);
+          if (ty == 0) {
+            if (kind_is_cyclic(sg.kind)) {  // (z_gn, z_1) closes the cycle
+              const float* zf = zbuf + (size_t)(sg.hoff - sg.gpos) * N + ic;
+              s0 += (double)pair_term<float>(sg.kind, zf[(size_t)(sg.gn - 1) * N], zf[0]);
+            }
+            Gs[c][tx] += finalize_f32(sg.kind, s0, s1, s2, pp, sg.gn);
           }
-          Gs[c][tx] += finalize_f32(sg.kind, s0, s1, s2, pp, sg.gn);
         }
         __syncthreads();
       }
@@ -1490,8 +1513,8 @@ cudaError_t launch_split(const MmaPlan& p, const Tables& tb, const Function& F, 
       e = launch_any(sp.mode[gi], p, tb, F, xs, n, out + r0, st, sp.list[gi], sp.nlist[gi], g,
                      d2, z);
     if (e == cudaSuccess) {
-      finish_kernel<<<(unsigned)((n + 31) / 32), dim3(32, kFinSlices), 0, st>>>(tb, F, z, g, d2,
-                                                                               n, out + r0);
+      finish_kernel<<<(unsigned)((n + kFinX - 1) / kFinX), dim3(kFinX, kFinSlices), 0, st>>>(
+          tb, F, z, g, d2, n, out + r0);
       e = cudaGetLastError();
     }
   }

@@ -277,7 +277,7 @@ eval_simt_f32_kernel(Tables tb, Function F, const float* __restrict__ x, int N,
       const int kind = sg.kind;
       const bool pairs = kind_has_pairs(kind);
       const float gnT = (float)sg.gn, off = (float)sg.offset;
-      const float kat_e = (kind == K_KATSUURA) ? (float)(10.0 / pow((double)sg.gn, 1.2)) : 0.f;
+      const float kat_e = sg.kat_e;
       const float* aux = tb.aux32 + (sg.aux_off >= 0 ? sg.aux_off : 0);
       const bool has_aux = sg.aux_off >= 0;
       for (int m = warp; m < BM; m += nwarps) {
