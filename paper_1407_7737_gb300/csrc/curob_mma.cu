@@ -285,18 +285,25 @@ __device__ __forceinline__ void epi_chunk_k(const float* v, int c, int cend, con
   st.p *= (double)part.p;
 }
 
+// kHeavy: the build that evaluates heavy kinds in the epilogue (no z
+// scratch); without it those kinds always go to the scratch, and their code,
+// with the registers it needs, stays out of the kernel.
+template <bool kHeavy>
 __device__ __forceinline__ void epi_chunk(int kind, const float* v, int c, int cend,
                                           const EpiSeg& es, EpiState& st) {
   switch (kind) {
 #define CUROB_EPI_CASE(K) \
   case K: epi_chunk_k<K>(v, c, cend, es, st); break;
+#define CUROB_EPI_HEAVY(K) \
+  case K: if constexpr (kHeavy) epi_chunk_k<K>(v, c, cend, es, st); break;
     CUROB_EPI_CASE(K_SPHERE) CUROB_EPI_CASE(K_ELLIPSOID) CUROB_EPI_CASE(K_ELLIPTIC)
-    CUROB_EPI_CASE(K_DISCUS) CUROB_EPI_CASE(K_CIGAR) CUROB_EPI_CASE(K_POWERS)
-    CUROB_EPI_CASE(K_SHARPV) CUROB_EPI_CASE(K_STEP) CUROB_EPI_CASE(K_WEIERSTRASS)
-    CUROB_EPI_CASE(K_GRIEWANK) CUROB_EPI_CASE(K_RASTRIGIN) CUROB_EPI_CASE(K_SCHAFFER7)
-    CUROB_EPI_CASE(K_EGR) CUROB_EPI_CASE(K_ROSENBROCK) CUROB_EPI_CASE(K_SCHWEFEL)
-    CUROB_EPI_CASE(K_KATSUURA) CUROB_EPI_CASE(K_LUNACEK) CUROB_EPI_CASE(K_ACKLEY)
-    CUROB_EPI_CASE(K_HAPPYCAT) CUROB_EPI_CASE(K_HGBAT) CUROB_EPI_CASE(K_SCHAFFER6)
+    CUROB_EPI_CASE(K_DISCUS) CUROB_EPI_CASE(K_CIGAR) CUROB_EPI_HEAVY(K_POWERS)
+    CUROB_EPI_CASE(K_SHARPV) CUROB_EPI_CASE(K_STEP) CUROB_EPI_HEAVY(K_WEIERSTRASS)
+    CUROB_EPI_HEAVY(K_GRIEWANK) CUROB_EPI_CASE(K_RASTRIGIN) CUROB_EPI_HEAVY(K_SCHAFFER7)
+    CUROB_EPI_HEAVY(K_EGR) CUROB_EPI_CASE(K_ROSENBROCK) CUROB_EPI_HEAVY(K_SCHWEFEL)
+    CUROB_EPI_HEAVY(K_KATSUURA) CUROB_EPI_CASE(K_LUNACEK) CUROB_EPI_CASE(K_ACKLEY)
+    CUROB_EPI_CASE(K_HAPPYCAT) CUROB_EPI_CASE(K_HGBAT) CUROB_EPI_HEAVY(K_SCHAFFER6)
+#undef CUROB_EPI_HEAVY
 #undef CUROB_EPI_CASE
     default: break;
   }
@@ -657,7 +664,11 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
                   make_uint4(lw[0], lw[1], lw[2], lw[3]);
             } else {
               // four integer slices of 128 y / sigma (exact in BF16),
-              // pre-scaled by their weight
+              // pre-scaled by their weight.  Every rounded value is at most
+              // ~129 in magnitude, where adding and subtracting 1.5 * 2^23
+              // rounds to the nearest integer, ties to even, exactly as
+              // rintf, with two full-rate additions
+              constexpr float kRnd = 12582912.0f;
               uint32_t w[4][4];
 #pragma unroll
               for (int qq = 0; qq < 4; ++qq) {
@@ -666,12 +677,13 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
                 for (int e = 0; e < 2; ++e) {
                   const int k = 2 * qq + e;
                   const float v = yh[k] * isig * 128.f;
-                  const float y1 = rintf(v);
+                  const float y1 = (v + kRnd) - kRnd;
                   const float v2 = ((v - y1) + yl[k] * isig * 128.f) * 256.f;
-                  const float y2 = rintf(v2);
+                  const float y2 = (v2 + kRnd) - kRnd;
                   const float v3 = (v2 - y2) * 256.f;
-                  const float y3 = rintf(v3);
-                  const float y4 = rintf((v3 - y3) * 256.f);
+                  const float y3 = (v3 + kRnd) - kRnd;
+                  const float v4 = (v3 - y3) * 256.f;
+                  const float y4 = (v4 + kRnd) - kRnd;
                   sl[e][0] = y1;
                   sl[e][1] = y2 * 0.00390625f;
                   sl[e][2] = y3 * 1.52587890625e-05f;
@@ -697,7 +709,7 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
     }
 }
 
-template <int kMode>
+template <int kMode, bool kHeavy>
 __device__ void epilogue_tile(const MmaArgs& a, const Smem& m, long long row0, RoleState& rs) {
   CUROB_ROLE_PROLOGUE
     // ------------------------------------------------------------- epilogue
@@ -768,7 +780,7 @@ __device__ void epilogue_tile(const MmaArgs& a, const Smem& m, long long row0, R
                   if (k < cend) zcol[(size_t)(c + k) * a.N] = v[k] * es.s + es.c0;
               }
             } else {
-              epi_chunk(kind, v, c, min(32, c_hi - c), es, st);
+              epi_chunk<kHeavy>(kind, v, c, min(32, c_hi - c), es, st);
             }
           }
           tc_fence_before();
@@ -899,11 +911,11 @@ __device__ void loader_tile(const MmaArgs& a, const Smem& m, long long row0, Rol
     __syncwarp();
 }
 
-template <int kMode>
+template <int kMode, bool kHeavy>
 __device__ inline void run_tile(const MmaArgs& a, const Smem& m, long long row0, RoleState& rs) {
   const int warp = threadIdx.x >> 5;
   if (warp < 8) producer_tile<kMode>(a, m, row0, rs);
-  else if (warp < 12) epilogue_tile<kMode>(a, m, row0, rs);
+  else if (warp < 12) epilogue_tile<kMode, kHeavy>(a, m, row0, rs);
   else if (warp == kMmaWarp) mma_tile<kMode>(a, m, row0, rs);
   else loader_tile<kMode>(a, m, row0, rs);
   if (*m.abort_flag) {  // no copy may still be landing when the CTA moves on or exits
@@ -921,13 +933,13 @@ __device__ inline void run_tile(const MmaArgs& a, const Smem& m, long long row0,
 }
 
 // One launch per function: CTA b evaluates candidates [128 b, 128 b + 128).
-template <int kMode>
+template <int kMode, bool kHeavy>
 __global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const Smem m = smem_map(smem_raw, args.nstage, args.stage_bytes);
   cta_setup(m, args.nstage);
   RoleState rs;
-  run_tile<kMode>(args, m, (long long)blockIdx.x * kTileM, rs);
+  run_tile<kMode, kHeavy>(args, m, (long long)blockIdx.x * kTileM, rs);
   cta_teardown(m);
 }
 
@@ -949,7 +961,7 @@ mma_batch_kernel(const MmaArgs* __restrict__ insts, const int2* __restrict__ wor
     const int w = *m.item;
     if (w >= nwork || *m.abort_flag) break;
     const int2 W = work[w];
-    run_tile<kMode>(insts[W.x], m, (long long)W.y * kTileM, rs);
+    run_tile<kMode, true>(insts[W.x], m, (long long)W.y * kTileM, rs);
     __syncthreads();  // outputs written; per-row tables free for the next item
   }
   cta_teardown(m);
@@ -1249,10 +1261,12 @@ cudaError_t launch_mode(const MmaPlan& p, const Tables& tb, const Function& F, c
   a.gout = gout;
   a.d2out = d2out;
   a.zbuf = zbuf;
-  cudaError_t e = cudaFuncSetAttribute(mma_eval_kernel<kMode>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // heavy kinds in the epilogue only when there is no z scratch for them
+  const bool heavy = zbuf == nullptr && F.hcols > 0;
+  const auto kern = heavy ? mma_eval_kernel<kMode, true> : mma_eval_kernel<kMode, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  mma_eval_kernel<kMode><<<(unsigned)((N + kTileM - 1) / kTileM), kThreads, smem, st>>>(a);
+  kern<<<(unsigned)((N + kTileM - 1) / kTileM), kThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
