@@ -330,7 +330,7 @@ def run_curob(args):
     # candidate); a heavy-kind member adds its z round trip through the
     # scratch (written by the tensor-core kernel, read by finish_kernel); a
     # MIXED composition reads x once per precision subset.
-    dram_per_call = {1: 111.7e6, 4: 125.6e6, 5: 332.1e6}
+    dram_per_call = {1: 108.8e6, 4: 123.2e6, 5: 321.4e6}
     traffic = dram_per_call.get(dom) if args.precision == "auto" else None
     roof = {"bound": "tensor" if dom != 3 else "alu", "kernel": mode_name[dom],
             "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",

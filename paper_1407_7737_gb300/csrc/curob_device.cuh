@@ -482,6 +482,10 @@ __device__ inline double finalize_f32(int kind, double a0, double a1, double a2,
   if (kind == K_HAPPYCAT) return pow(fabs(a0), 0.25) + 0.5 * a1 / gn;
   if (kind == K_HGBAT) return sqrt(fabs(a0 * a2)) + 0.5 * a1 / gn;
   if (kind == K_SCHWEFEL) return a0;  // the terms already hold 418.9829 - g1
+  // Weierstrass constant in closed form: cos(2 pi 3^k / 2) = cos(pi 3^k) = -1
+  // (3^k is odd), so sum_{k=0}^{20} 2^-k cos(...) = -(2 - 2^-20); the FP64
+  // path evaluates the printed series (21 FP64 cosines per candidate).
+  if (kind == K_WEIERSTRASS) return a0 + gn * (2.0 - 0x1p-20);
   return finalize(kind, a0, a1, a2, p, gn_i);
 }
 

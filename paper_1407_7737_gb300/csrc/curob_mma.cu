@@ -560,30 +560,43 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
         // operand's swizzle.  Lanes walk rows' (sorted) columns, so one
         // instruction touches a few rows' few sectors; each thread's copies
         // arrive on gbar[stage] when they land.
-        const float* xbase = a.x;
-        const long long nrows = a.N;
         const int nst = a.nstage, sbytes = a.stage_bytes, nvalid = sg.n;
+        // Per lane: column i of the half and rows rb + v kRowsPerInst.  Both
+        // swizzles repeat every 8 rows, so kPer offsets give every row's
+        // destination; source offsets are 32-bit within the tile; vmask has
+        // bit v for rows inside the batch.
+        constexpr int kRowsPerInst = 32 / kHalf;            // 4 (16-column stages) or 2
+        constexpr int kNv = 32 / kRowsPerInst;               // gathers per lane per stage
+        constexpr int kPer = 8 / kRowsPerInst;               // swizzle period in v
+        const int gi = lane % kHalf;                         // column of the half
+        const int rb = (warp & 3) * 32 + lane / kHalf;
+        const uint32_t dbyte = (uint32_t)((h * kCpp + (gi / 4) % kCpp) * 16 + (gi % 4) * 4);
+        const uint32_t dpo = (uint32_t)(((gi / 4) / kCpp) * kPart);
+        uint32_t dsw[kPer];
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) dsw[u] = dpo + swz_m<kMode>((uint32_t)(rb + u * kRowsPerInst), dbyte);
+        const float* xtile = a.x + row0 * (long long)D;
+        const int roff = rb * D, rstep = kRowsPerInst * D;
+        const long long nleft = a.N - row0;
+        uint32_t vmask = 0;
+#pragma unroll
+        for (int v = 0; v < kNv; ++v)
+          if (rb + v * kRowsPerInst < nleft) vmask |= 1u << v;
         auto issue = [=](int q) -> bool {
           const uint32_t g = it0 + (uint32_t)q;
           const int stage = g % nst;
           if (!mbar_wait(&empty[stage], ((g / nst) & 1u) ^ 1u, abort_flag, tb.status))
             return false;
-          uint8_t* A = stages + (size_t)stage * sbytes;
+          const uint32_t A = smem_u32(stages + (size_t)stage * sbytes);
           const int t = q % nslab;
-          constexpr int kRowsPerInst = 32 / kHalf;          // 4 (16-column stages) or 2
-          const int i = lane % kHalf;                       // column of the half
-          const int j = t * kKs + h * kHalf + i;
-          const bool cin = j < nvalid;
-          const int col = cin ? tabS[j] : 0;
-          const uint32_t dpart = smem_u32(A) + (uint32_t)(((i / 4) / kCpp) * kPart);
-          const uint32_t dbyte = (uint32_t)((h * kCpp + (i / 4) % kCpp) * 16 + (i % 4) * 4);
-#pragma unroll 4
-          for (int v = 0; v < 32 / kRowsPerInst; ++v) {
-            const int rr = (warp & 3) * 32 + v * kRowsPerInst + lane / kHalf;
-            const long long gr = row0 + rr;
-            const bool in = cin && gr < nrows;
-            const float* src = in ? xbase + gr * (long long)D + col : xbase;
-            const uint32_t dst = dpart + swz_m<kMode>((uint32_t)rr, dbyte);
+          const int j = t * kKs + h * kHalf + gi;
+          const uint32_t m = j < nvalid ? vmask : 0u;  // invalid copies fill zeros
+          const float* xc = xtile + (j < nvalid ? tabS[j] : 0);
+#pragma unroll
+          for (int v = 0; v < kNv; ++v) {
+            const bool in = (m >> v) & 1u;
+            const float* src = in ? xc + (roff + v * rstep) : xtile;
+            const uint32_t dst = A + dsw[v % kPer] + (uint32_t)((v / kPer) * 8 * kRow);
             asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src),
                          "r"(in ? 4 : 0)
                          : "memory");
@@ -630,12 +643,10 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
             for (int e = 0; e < kPer; ++e) {
               const int il = cc * kPer + e;  // column within the half
               const int j = t * kKs + h * kHalf + il;
-              // branch-free, so that the chunk's elements interleave
-              float hh, ll;
-              shift_ff(xv[il], tabH[j], tabL[j], hh, ll);
-              const bool valid = vrow && j < nvalid;
-              yh[e] = valid ? hh : 0.f;
-              yl[e] = valid ? ll : 0.f;
+              // branch-free, so that the chunk's elements interleave.  A
+              // column past the block has x = 0 (zero-filled copy) and o = 0
+              // (staged), so y = 0; a row past the batch is never written.
+              shift_ff(xv[il], tabH[j], tabL[j], yh[e], yl[e]);
               d2p = fmaf(yh[e], yh[e], d2p);
             }
             const uint32_t off = swz_m<kMode>((uint32_t)r, (uint32_t)(c * 16));
