@@ -638,15 +638,21 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
 #pragma unroll
           for (int cc = 0; cc < kCpp; ++cc) {
             const int c = h * kCpp + cc;  // chunk of the row
-            float yh[kPer], yl[kPer];
+            float yh[kPer], yl[kPer], oh[kPer], ol[kPer];
+            const int jc = t * kKs + h * kHalf + cc * kPer;  // first column of the chunk
+#pragma unroll
+            for (int q4 = 0; q4 < kPer / 4; ++q4) {  // o words, 16 bytes at a time
+              const float4 a4 = *reinterpret_cast<const float4*>(tabH + jc + 4 * q4);
+              const float4 b4 = *reinterpret_cast<const float4*>(tabL + jc + 4 * q4);
+              oh[4 * q4] = a4.x; oh[4 * q4 + 1] = a4.y; oh[4 * q4 + 2] = a4.z; oh[4 * q4 + 3] = a4.w;
+              ol[4 * q4] = b4.x; ol[4 * q4 + 1] = b4.y; ol[4 * q4 + 2] = b4.z; ol[4 * q4 + 3] = b4.w;
+            }
 #pragma unroll
             for (int e = 0; e < kPer; ++e) {
-              const int il = cc * kPer + e;  // column within the half
-              const int j = t * kKs + h * kHalf + il;
               // branch-free, so that the chunk's elements interleave.  A
               // column past the block has x = 0 (zero-filled copy) and o = 0
               // (staged), so y = 0; a row past the batch is never written.
-              shift_ff(xv[il], tabH[j], tabL[j], yh[e], yl[e]);
+              shift_ff(xv[cc * kPer + e], oh[e], ol[e], yh[e], yl[e]);
               d2p = fmaf(yh[e], yh[e], d2p);
             }
             const uint32_t off = swz_m<kMode>((uint32_t)r, (uint32_t)(c * 16));
@@ -674,12 +680,14 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
               *reinterpret_cast<uint4*>(A + kPart + off) =
                   make_uint4(lw[0], lw[1], lw[2], lw[3]);
             } else {
-              // four integer slices of 128 y / sigma (exact in BF16),
-              // pre-scaled by their weight.  Every rounded value is at most
-              // ~129 in magnitude, where adding and subtracting 1.5 * 2^23
-              // rounds to the nearest integer, ties to even, exactly as
-              // rintf, with two full-rate additions
-              constexpr float kRnd = 12582912.0f;
+              // four slices of v = 128 y / sigma (exact in BF16), already at
+              // their weight: s1 = rint(v), then the remainder r = v - s1
+              // (plus y's low word) rounded to multiples of 2^-8, 2^-16 and
+              // 2^-24 in turn.  Adding and subtracting 1.5 * 2^(23 - 8a)
+              // rounds to a multiple of 2^-8a, ties to even, exactly as rintf
+              // of the 2^8a-scaled value does (|v| < 128, |r| <= 2^-1, 2^-9,
+              // 2^-17), and every remainder is exact
+              const float s128 = isig * 128.f;
               uint32_t w[4][4];
 #pragma unroll
               for (int qq = 0; qq < 4; ++qq) {
@@ -687,18 +695,18 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                   const int k = 2 * qq + e;
-                  const float v = yh[k] * isig * 128.f;
-                  const float y1 = (v + kRnd) - kRnd;
-                  const float v2 = ((v - y1) + yl[k] * isig * 128.f) * 256.f;
-                  const float y2 = (v2 + kRnd) - kRnd;
-                  const float v3 = (v2 - y2) * 256.f;
-                  const float y3 = (v3 + kRnd) - kRnd;
-                  const float v4 = (v3 - y3) * 256.f;
-                  const float y4 = (v4 + kRnd) - kRnd;
+                  const float v = yh[k] * s128;
+                  const float y1 = (v + 12582912.0f) - 12582912.0f;       // 1.5 * 2^23
+                  float rr = fmaf(yl[k], s128, v - y1);
+                  const float y2 = (rr + 49152.0f) - 49152.0f;            // 1.5 * 2^15
+                  rr = rr - y2;
+                  const float y3 = (rr + 192.0f) - 192.0f;                // 1.5 * 2^7
+                  rr = rr - y3;
+                  const float y4 = (rr + 0.75f) - 0.75f;                  // 1.5 * 2^-1
                   sl[e][0] = y1;
-                  sl[e][1] = y2 * 0.00390625f;
-                  sl[e][2] = y3 * 1.52587890625e-05f;
-                  sl[e][3] = y4 * 5.9604644775390625e-08f;
+                  sl[e][1] = y2;
+                  sl[e][2] = y3;
+                  sl[e][3] = y4;
                 }
 #pragma unroll
                 for (int pp = 0; pp < 4; ++pp) w[pp][qq] = pack_bf16(sl[0][pp], sl[1][pp]);
