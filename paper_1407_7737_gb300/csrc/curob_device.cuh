@@ -143,6 +143,14 @@ __host__ __device__ constexpr bool kind_has_pairs(int k) {
   return k == K_SCHAFFER7 || k == K_EGR || k == K_ROSENBROCK || k == K_SCHAFFER6;
 }
 __host__ __device__ inline bool kind_is_cyclic(int k) { return k == K_EGR || k == K_SCHAFFER6; }
+// Which of a1, a2 and p a kind's FP32 terms touch (a0 is always a sum);
+// the others stay 0 or 1, so their FP64 accumulation can be skipped.
+__host__ __device__ constexpr bool kind_uses_a1(int k) {
+  return k == K_DISCUS || k == K_CIGAR || k == K_SHARPV || k == K_LUNACEK || k == K_ACKLEY ||
+         k == K_HAPPYCAT || k == K_HGBAT;
+}
+__host__ __device__ constexpr bool kind_uses_a2(int k) { return k == K_LUNACEK || k == K_HGBAT; }
+__host__ __device__ constexpr bool kind_uses_p(int k) { return k == K_GRIEWANK || k == K_KATSUURA; }
 __host__ __device__ inline bool kind_is_sensitive(int k) {
   return k == K_DISCUS || k == K_WEIERSTRASS || k == K_EGR || k == K_KATSUURA;
 }

@@ -279,10 +279,10 @@ __device__ __forceinline__ void epi_chunk_k(const float* v, int c, int cend, con
     }
     st.zprev = zprev;
   }
-  st.a0 += (double)part.a0;
-  st.a1 += (double)part.a1;
-  st.a2 += (double)part.a2;
-  st.p *= (double)part.p;
+  st.a0 += (double)part.a0;  // FP64 operations only for the fields the kind uses
+  if constexpr (kind_uses_a1(KIND)) st.a1 += (double)part.a1;
+  if constexpr (kind_uses_a2(KIND)) st.a2 += (double)part.a2;
+  if constexpr (kind_uses_p(KIND)) st.p *= (double)part.p;
 }
 
 // kHeavy: the build that evaluates heavy kinds in the epilogue (no z
@@ -1159,13 +1159,21 @@ __device__ __forceinline__ void fin_dispatch(int kind, const float* zc, long lon
   }
 }
 
-__device__ __forceinline__ void fin_warp_sum(double& a0, double& a1, double& a2, double& p) {
+// Heavy kinds accumulate only a sum (a0) and a product (p): kind_uses_a1 and
+// kind_uses_a2 are false for all of them.
+static_assert(!kind_uses_a1(K_POWERS) && !kind_uses_a1(K_WEIERSTRASS) && !kind_uses_a1(K_GRIEWANK) &&
+                  !kind_uses_a1(K_SCHAFFER7) && !kind_uses_a1(K_EGR) && !kind_uses_a1(K_SCHWEFEL) &&
+                  !kind_uses_a1(K_KATSUURA) && !kind_uses_a1(K_SCHAFFER6) &&
+                  !kind_uses_a2(K_POWERS) && !kind_uses_a2(K_WEIERSTRASS) &&
+                  !kind_uses_a2(K_GRIEWANK) && !kind_uses_a2(K_SCHAFFER7) && !kind_uses_a2(K_EGR) &&
+                  !kind_uses_a2(K_SCHWEFEL) && !kind_uses_a2(K_KATSUURA) && !kind_uses_a2(K_SCHAFFER6),
+              "heavy kinds use a0 and p only");
+
+__device__ __forceinline__ void fin_warp_sum(double& a0, double& p) {
   // lanes tx, tx + kFinX, ... of a warp hold the same candidate
 #pragma unroll
   for (int off = kFinX; off < 32; off <<= 1) {
     a0 += __shfl_xor_sync(0xffffffffu, a0, off);
-    a1 += __shfl_xor_sync(0xffffffffu, a1, off);
-    a2 += __shfl_xor_sync(0xffffffffu, a2, off);
     p *= __shfl_xor_sync(0xffffffffu, p, off);
   }
 }
@@ -1175,7 +1183,7 @@ finish_kernel(Tables tb, Function F, const float* zbuf, const double* gout, cons
               int N, float* out) {
   constexpr int kWarps = kFinX * kFinSlices / 32;
   constexpr int kSlicesPerWarp = 32 / kFinX;
-  __shared__ double red[4][kWarps][kFinX];
+  __shared__ double red[2][kWarps][kFinX];
   __shared__ double Gs[kMaxComponents][kFinX];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int warp = ty / kSlicesPerWarp;
@@ -1184,14 +1192,14 @@ finish_kernel(Tables tb, Function F, const float* zbuf, const double* gout, cons
   const long long ic = valid ? i : 0;  // rows past N read row 0 and write nothing
   if (ty == 0)
     for (int c = 0; c < F.ncomp; ++c) Gs[c][tx] = gout[(size_t)c * N + ic];
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, p = 1.0;
+  double a0 = 0.0, p = 1.0;
   for (int c = 0; c < F.ncomp; ++c) {
     const Component Cm = tb.comp[F.comp0 + c];
     for (int si = 0; si < Cm.nseg; ++si) {
       const Segment sg = tb.seg[Cm.seg0 + si];
       if (sg.hoff < 0) continue;  // block-uniform: every thread takes the same path
       if (sg.gfirst) {
-        a0 = a1 = a2 = 0.0;
+        a0 = 0.0;
         p = 1.0;
       }
       const int L = (sg.n + kFinSlices - 1) / kFinSlices;
@@ -1201,34 +1209,28 @@ finish_kernel(Tables tb, Function F, const float* zbuf, const double* gout, cons
       Acc<float> acc = acc_zero<float>();
       fin_dispatch(sg.kind, zc, N, j0, j1, sg.gpos, (float)sg.gn, aux, sg.kat_e, acc);
       a0 += (double)acc.a0;
-      a1 += (double)acc.a1;
-      a2 += (double)acc.a2;
-      p *= (double)acc.p;
+      if (kind_uses_p(sg.kind)) p *= (double)acc.p;
       if (sg.glast) {
-        fin_warp_sum(a0, a1, a2, p);
+        fin_warp_sum(a0, p);
         if (ty % kSlicesPerWarp == 0) {
           red[0][warp][tx] = a0;
-          red[1][warp][tx] = a1;
-          red[2][warp][tx] = a2;
-          red[3][warp][tx] = p;
+          red[1][warp][tx] = p;
         }
         __syncthreads();
-        if (warp == 0) {  // lane (tx, q): warps q, q + 4, ...; then across q
+        if (warp == 0) {  // lane (tx, q): warps q, q + kSlicesPerWarp, ...; then across q
           const int q = ty % kSlicesPerWarp;
-          double s0 = 0.0, s1 = 0.0, s2 = 0.0, pp = 1.0;
+          double s0 = 0.0, pp = 1.0;
           for (int w = q; w < kWarps; w += kSlicesPerWarp) {
             s0 += red[0][w][tx];
-            s1 += red[1][w][tx];
-            s2 += red[2][w][tx];
-            pp *= red[3][w][tx];
+            pp *= red[1][w][tx];
           }
-          fin_warp_sum(s0, s1, s2, pp);
+          fin_warp_sum(s0, pp);
           if (ty == 0) {
             if (kind_is_cyclic(sg.kind)) {  // (z_gn, z_1) closes the cycle
               const float* zf = zbuf + (size_t)(sg.hoff - sg.gpos) * N + ic;
               s0 += (double)pair_term<float>(sg.kind, zf[(size_t)(sg.gn - 1) * N], zf[0]);
             }
-            Gs[c][tx] += finalize_f32(sg.kind, s0, s1, s2, pp, sg.gn);
+            Gs[c][tx] += finalize_f32(sg.kind, s0, 0.0, 0.0, pp, sg.gn);
           }
         }
         __syncthreads();
