@@ -100,8 +100,16 @@ curob_status curob_evaluate(int fid, const double* x, int N, double* out, curob_
 /* Sec. 1.3, func_evaluatef(): the same with FP32 x and out.  The shift x - o
  * is taken in FP64 (o is FP64), the block rotation runs on the tensor cores
  * in the precision set by curob_set_precision, reductions are carried in
- * FP64 across lanes.  Same errors as curob_evaluate, plus UNSUPPORTED if a
- * forced precision cannot handle the instance's block sizes. */
+ * FP64 across lanes.  A function with a block of a heavy kind (see
+ * curob_query_launches), or a MIXED composition, takes a second kernel on
+ * the same stream, with scratch (4 bytes per heavy variable and 80 bytes
+ * per candidate, at most 256 MB, candidates in slices beyond that) taken
+ * stream-ordered from a pool the library keeps; calls on different streams
+ * may run concurrently.  If that scratch cannot be had, a function with one
+ * precision group falls back to the single fused launch, and a MIXED
+ * composition returns CUDA.  Same errors as curob_evaluate, plus
+ * UNSUPPORTED if a forced precision cannot handle the instance's block
+ * sizes. */
 curob_status curob_evaluatef(int fid, const float* x, int N, float* out, curob_stream_t stream);
 
 /* Sec. 1.3, h_func_evaluate / h_func_evaluatef: host-pointer wrappers.
