@@ -368,7 +368,7 @@ def run_curob(args):
     # candidate); a heavy-kind member adds its z round trip through the
     # scratch (written by the tensor-core kernel, read by finish_kernel); a
     # MIXED composition reads x once per precision subset.
-    dram_per_call = {1: 106.9e6, 4: 123.9e6, 5: 323.3e6}
+    dram_per_call = {1: 106.2e6, 4: 122.9e6, 5: 324.4e6}
     traffic = dram_per_call.get(dom) if args.precision == "auto" else None
     roof = {"bound": "tensor" if dom != 3 else "alu", "kernel": mode_name[dom],
             "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",

@@ -144,6 +144,13 @@ struct MmaArgs {
   double* d2out;               // ([kMaxComponents][N] each), closed by finish_kernel
   float* zbuf;                 // heavy-kind z, variable-major ([F.hcols][N]); nullptr: the
                                // epilogue evaluates heavy kinds itself
+  // Accumulator regions: hand-offs alternate between TMEM columns [0, W) and
+  // [acc_hi, acc_hi + W) (acc_hi = T - W, T = 512, or 256 per EXACT
+  // accumulator; W a multiple of 32 >= every hand-off's width), so the two
+  // overlap in acc_ovl = 2 W - T columns (<= 0: none) and only those must be
+  // drained before the next hand-off may start.
+  int acc_hi;
+  int acc_ovl;
 };
 
 // Floats reserved per block for each precision's image (the TF32 size; BF16
@@ -777,34 +784,63 @@ __device__ void epilogue_tile(const MmaArgs& a, const Smem& m, long long row0, R
           tc_fence_after();
           const int c_lo = kMode == M_EXACT ? cc * nw : 0;
           const int c_hi = kMode == M_EXACT ? min(sg.n, c_lo + nw) : sg.n;
-          for (int c = c_lo; c < c_hi; c += 32) {
-            float v[32];
-            if constexpr (kMode == M_EXACT) {
-              float g1[32];
-              const uint32_t lc = (uint32_t)(c - c_lo);
-              tmem_ld32(t_lane + lc, v);
-              tmem_ld32(t_lane + kExactAcc1 + lc, g1);
-              const float base = sig * 6.103515625e-05f;  // sigma 2^-14
-#pragma unroll
-              for (int k = 0; k < 32; ++k)
-                v[k] = (c + k < c_hi) ? (v[k] + g1[k]) * (base * tau[c + k]) : 0.f;
-            } else {
-              tmem_ld32(t_lane + (uint32_t)c, v);
-            }
-            if (zout) {
-              if (grow < a.N) {
-                const int cend = min(32, c_hi - c);
+          const bool odd = (chunk_it & 1u) != 0;
+          const uint32_t ab = odd ? (uint32_t)a.acc_hi : 0u;  // TMEM column of local column 0
+          // local columns [l0, l1) of this hand-off, 32 at a time
+          auto drain = [&](int l0, int l1) {
+            for (int l = l0; l < l1; l += 32) {
+              const int c = c_lo + l;
+              const int cend = min(32, l1 - l);
+              float v[32];
+              if constexpr (kMode == M_EXACT) {
+                float g1[32];
+                tmem_ld32(t_lane + ab + (uint32_t)l, v);
+                tmem_ld32(t_lane + kExactAcc1 + ab + (uint32_t)l, g1);
+                const float base = sig * 6.103515625e-05f;  // sigma 2^-14
 #pragma unroll
                 for (int k = 0; k < 32; ++k)
-                  if (k < cend) zcol[(size_t)(c + k) * a.N] = v[k] * es.s + es.c0;
+                  v[k] = (k < cend) ? (v[k] + g1[k]) * (base * tau[c + k]) : 0.f;
+              } else {
+                tmem_ld32(t_lane + ab + (uint32_t)l, v);
               }
-            } else {
-              epi_chunk<kHeavy>(kind, v, c, min(32, c_hi - c), es, st);
+              if (zout) {
+                if (grow < a.N) {
+#pragma unroll
+                  for (int k = 0; k < 32; ++k)
+                    if (k < cend) zcol[(size_t)(c + k) * a.N] = v[k] * es.s + es.c0;
+                }
+              } else {
+                epi_chunk<kHeavy>(kind, v, c, cend, es, st);
+              }
             }
+          };
+          auto release = [&]() {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tmem_empty);
+          };
+          const int w = c_hi - c_lo;
+          // Columns the next hand-off's region covers go first, then the
+          // accumulator is released and the rest drains under the next
+          // block's MMAs.  Pair kinds (a chain over consecutive columns) and
+          // the fused build keep column order and release at the end.
+          if (zout || (!kHeavy && !kind_has_pairs(kind))) {
+            int f0, f1;  // local range shared with the next hand-off's region
+            if (odd) {
+              f0 = 0;
+              f1 = max(0, min(w, a.acc_ovl));
+            } else {
+              f0 = min(w, a.acc_hi);
+              f1 = w;
+            }
+            drain(f0, f1);
+            release();
+            drain(0, f0);
+            drain(f1, w);
+          } else {
+            drain(0, w);
+            release();
           }
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(tmem_empty);
         }
         if (ok && sg.glast && !zout) gsum += st.close(kind, sg.gn);
       }
@@ -840,6 +876,7 @@ __device__ void mma_tile(const MmaArgs& a, const Smem& m, long long row0, RoleSt
               break;
             }
             tc_fence_after();
+            const uint32_t ab = (chunk_it & 1u) ? (uint32_t)a.acc_hi : 0u;  // accumulator region
             for (int t = 0; t < nslab; ++t, ++it) {
               const int stage = it % a.nstage;
               const uint32_t ph = (it / a.nstage) & 1u;
@@ -862,7 +899,7 @@ __device__ void mma_tile(const MmaArgs& a, const Smem& m, long long row0, RoleSt
                   constexpr int kPb[10] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
 #pragma unroll
                   for (int pq = 0; pq < 10; ++pq) {
-                    const uint32_t dt = tmem_base + (pq == 0 ? 0u : (uint32_t)kExactAcc1);
+                    const uint32_t dt = tmem_base + ab + (pq == 0 ? 0u : (uint32_t)kExactAcc1);
                     const uint64_t da = sdesc_m<kMode>(sa + kPa[pq] * kPart + ko);
                     const uint64_t db = sdesc_m<kMode>(sb + kPb[pq] * bpart + ko);
                     tc_mma<false>(dt, da, db, id0, (pq <= 1) ? first : 1u);
@@ -872,7 +909,7 @@ __device__ void mma_tile(const MmaArgs& a, const Smem& m, long long row0, RoleSt
                   for (int h = 0; h < (n1 > 0 ? 2 : 1); ++h) {
                     const uint32_t boff = (uint32_t)(h * n0 * kRow) + ko;
                     const uint64_t dbh = sdesc_m<kMode>(sb + boff), dbl = sdesc_m<kMode>(sb + bpart + boff);
-                    const uint32_t dt = tmem_base + (uint32_t)(h * n0);
+                    const uint32_t dt = tmem_base + ab + (uint32_t)(h * n0);
                     const uint32_t idd = h ? id1 : id0;
                     tc_mma<kMode == M_TF32>(dt, dah, dbh, idd, first);
                     tc_mma<kMode == M_TF32>(dt, dah, dbl, idd, 1u);
@@ -1252,6 +1289,17 @@ finish_kernel(Tables tb, Function F, const float* zbuf, const double* gout, cons
   out[i] = (float)(f + kFopt);
 }
 
+// Accumulator regions of a launch (MmaArgs::acc_hi, acc_ovl): EXACT hand-offs
+// are at most kExactMaxNC wide in each 256-column half of TMEM; the others are
+// a whole block, npad_max rounded up to 32, in all 512 columns.
+template <int kMode>
+void set_acc_regions(MmaArgs& a, int npad_max) {
+  const int T = kMode == M_EXACT ? kExactAcc1 : kMaxNpad;
+  const int W = kMode == M_EXACT ? kExactMaxNC : std::min(kMaxNpad, (npad_max + 31) / 32 * 32);
+  a.acc_hi = T - W;
+  a.acc_ovl = 2 * W - T;
+}
+
 template <int kMode>
 cudaError_t launch_mode(const MmaPlan& p, const Tables& tb, const Function& F, const float* x,
                         int N, float* out, cudaStream_t st, const int* list = nullptr,
@@ -1282,6 +1330,7 @@ cudaError_t launch_mode(const MmaPlan& p, const Tables& tb, const Function& F, c
   a.gout = gout;
   a.d2out = d2out;
   a.zbuf = zbuf;
+  set_acc_regions<kMode>(a, npad_max);
   // heavy kinds in the epilogue only when there is no z scratch for them
   const bool heavy = zbuf == nullptr && F.hcols > 0;
   const auto kern = heavy ? mma_eval_kernel<kMode, true> : mma_eval_kernel<kMode, false>;
@@ -1455,6 +1504,7 @@ void mma_fill_args(void* dst, const MmaPlan& p, const Tables& tb, const Function
   a.gout = nullptr;
   a.d2out = nullptr;
   a.zbuf = nullptr;
+  set_acc_regions<M_EXACT>(a, npad_of(F.max_n));
   memcpy(dst, &a, sizeof(a));
 }
 
