@@ -48,7 +48,10 @@
 //              (cp.async.bulk, the TMA engine).
 // Stages rotate through shared memory under full/empty mbarriers; the
 // accumulators are handed from the MMA warp to the epilogue and back under
-// tmem_full/tmem_empty.  Every wait is bounded: past ~2 s it raises
+// tmem_full/tmem_empty, alternating between the low and the high end of
+// TMEM: the epilogue drains the columns the next accumulator will overwrite,
+// hands TMEM back, and drains the rest while the next block's MMAs run
+// (MmaArgs::acc_hi / acc_ovl).  Every wait is bounded: past ~2 s it raises
 // DEV_TIMEOUT in the status word, the CTA stops, and TMEM is freed before
 // exit.
 #include <cuda_bf16.h>
