@@ -56,6 +56,9 @@ def parse():
                     help="training samples and pool size of the pre-screen measurement")
     ap.add_argument("--streams", type=int, default=8,
                     help="streams the step's 37 independent calls are spread over (1: one stream)")
+    ap.add_argument("--paper-protocol", action="store_true",
+                    help="the paper's small-batch timing (N = 50 per call, D in 10/32/64/96, FP32 and "
+                         "FP64, against the oracle on one core): one JSON line, no benchmark line")
     ap.add_argument("--profile-fid", type=int, default=None,
                     help="profiling case: two launches of one function, no JSON")
     return ap.parse_args()
@@ -685,9 +688,73 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_paper_protocol(args, runs=1000, oracle_runs=3):
+    """Sec. 1.4's timing: N = 50 candidates per call, every function at D =
+    10, 32, 64, 96, FP32 (curob_evaluatef, AUTO) and FP64 (curob_evaluate),
+    each call repeated `runs` times back to back on one stream (CUDA events),
+    against the FP64 oracle on one host core (its instance setup excluded).
+    Speedup per function = oracle time / GPU time per call; reported per D as
+    the mean over the functions defined at that D."""
+    import torch
+    import oracle
+    from paper_1407_7737_gb300 import binding as cu
+    from paper_1407_7737_gb300 import inputs
+    n = 50
+    stream = torch.cuda.current_stream()
+    per_d = {}
+    for d in (10, 32, 64, 96):
+        cu.curob_initialize(d, n, SEED)
+        x64h = inputs.uniform(n, d, 900 + d)
+        x64 = torch.from_numpy(x64h).cuda()
+        x32 = x64.float()
+        o64 = torch.empty(n, dtype=torch.float64, device="cuda")
+        o32 = torch.empty(n, dtype=torch.float32, device="cuda")
+        rows = []
+        for fid in range(NFUN):
+            try:
+                cu.curob_query_precision(fid)
+            except cu.CurobError:
+                continue  # not defined at this D
+            times = []
+            for call, xx, oo in ((cu.curob_evaluatef, x32, o32), (cu.curob_evaluate, x64, o64)):
+                for _ in range(5):
+                    call(fid, xx, n, oo, stream)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(runs):
+                    call(fid, xx, n, oo, stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b) * 1e3 / runs)  # us per call
+            comps = oracle.generate(fid, d, SEED)
+            oracle.evaluate_given(fid, d, comps, x64h, nthreads=1)
+            t = time.perf_counter()
+            for _ in range(oracle_runs):
+                oracle.evaluate_given(fid, d, comps, x64h, nthreads=1)
+            t_cpu = (time.perf_counter() - t) * 1e6 / oracle_runs
+            rows.append((fid, times[0], times[1], t_cpu))
+        cu.curob_get_device_status(stream)
+        cu.curob_dispose()
+        r = np.array([[f32, f64, cpu] for _, f32, f64, cpu in rows])
+        per_d[str(d)] = {
+            "functions": len(rows),
+            "f32_us_per_call_mean": round(float(r[:, 0].mean()), 2),
+            "f64_us_per_call_mean": round(float(r[:, 1].mean()), 2),
+            "oracle_us_per_call_mean": round(float(r[:, 2].mean()), 1),
+            "speedup_f32_mean": round(float((r[:, 2] / r[:, 0]).mean()), 1),
+            "speedup_f64_mean": round(float((r[:, 2] / r[:, 1]).mean()), 1),
+            "per_function": [{"fid": f, "f32_us": round(a, 2), "f64_us": round(b, 2),
+                              "oracle_us": round(c, 1)} for f, a, b, c in rows]}
+    print(json.dumps({"protocol": "paper small-batch timing (N = 50 per call)", "runs": runs,
+                      "oracle": "FP64 oracle, 1 host core", "per_D": per_d}))
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.paper_protocol:
+        run_paper_protocol(a)
     else:
         run_curob(a)
