@@ -56,6 +56,9 @@ def parse():
                     help="training samples and pool size of the pre-screen measurement")
     ap.add_argument("--streams", type=int, default=8,
                     help="streams the step's 37 independent calls are spread over (1: one stream)")
+    ap.add_argument("--order", default="longest", choices=["longest", "fid"],
+                    help="issue order of the step's calls over the streams: longest first (per-call "
+                         "times measured during warm-up) or function ID")
     ap.add_argument("--paper-protocol", action="store_true",
                     help="the paper's small-batch timing (N = 50 per call, D in 10/32/64/96, FP32 and "
                          "FP64, against the oracle on one core): one JSON line, no benchmark line")
@@ -232,13 +235,15 @@ def run_curob(args):
     S = max(1, args.streams)
     side = [torch.cuda.Stream(dev) for _ in range(S)] if S > 1 else []
 
+    order = list(range(NFUN))  # issue order of the calls (longest first after warm-up)
+
     def step_streams():
         fork = torch.cuda.Event()
         fork.record(stream)
         for sd in side:
             sd.wait_event(fork)
-        for fid in range(NFUN):
-            cu.curob_evaluatef(fid, X[fid], N, OUT[fid], side[fid % S])
+        for k, fid in enumerate(order):
+            cu.curob_evaluatef(fid, X[fid], N, OUT[fid], side[k % S])
         for sd in side:
             join = torch.cuda.Event()
             join.record(sd)
@@ -249,6 +254,18 @@ def run_curob(args):
         timed_step()
     torch.cuda.synchronize()
     cu.curob_get_device_status(stream)
+    if S > 1 and args.order == "longest":
+        # one warm-up step on one stream with every call timed; the timed
+        # steps then issue the calls longest first, so that the short ones
+        # fill the streams' tails (the work is the same 37 calls)
+        wev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(NFUN)]
+        step(wev)
+        torch.cuda.synchronize()
+        wt = [wev[f][0].elapsed_time(wev[f][1]) for f in range(NFUN)]
+        order[:] = sorted(range(NFUN), key=lambda f: -wt[f])
+        timed_step()
+        torch.cuda.synchronize()
 
     barrier(pg)
     torch.cuda.synchronize()
@@ -457,7 +474,8 @@ def run_curob(args):
                        "l2": "37 distinct input batches (2.4 GB) > L2 per step",
                        "streams": S,
                        "step": f"37 curob_evaluatef calls, round-robin over {S} stream(s) "
-                               "forked from and joined into the timing stream",
+                               "forked from and joined into the timing stream"
+                               + (", longest first" if S > 1 and args.order == "longest" else ""),
                        "parallelism": f"replicas x{world} (independent batches)"},
             "one_stream_ms_per_step": round(ms_seq, 4),
             "one_stream_evals_s": round(NFUN * N / (ms_seq / 1e3), 1),
