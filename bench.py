@@ -649,7 +649,7 @@ def ragged_batch(cu, torch, dev, stream, reps=5, n_items=64, seed=2024):
 
 
 def cpu_baseline(sample_n=8, budget_s=25.0):
-    """The FP64 oracle on the machine's host cores: every function on sample_n
+    """The FP64 oracle on the host's cores: every function on sample_n
     candidates of the D = 1000 workload (bounded to ~budget_s of CPU work)."""
     import oracle
     from paper_1407_7737_gb300 import inputs

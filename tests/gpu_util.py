@@ -1,8 +1,9 @@
 """Helpers for the GPU tests: library (re)initialisation, loading the oracle's
 instance into the library, and the tolerance rules.
 
-Tolerances (derived in the design doc from the arithmetic):
-  FP64 path   |f_gpu - f_ref| <= 1e-12 |f_ref|
+Tolerances:
+  FP64 path   |f_gpu - f_ref| <= 1e-12 |f_ref|  (same FP64 arithmetic; only the
+              summation order and the rotation's accumulation differ)
   FP32 paths  |f_gpu - f_ref| <= max(1e-5 |f_ref|, 1e-6 f_scale), f_ref the
               oracle at the FP32-rounded x, f_scale = median |f - f_opt| over
               uniform candidates of the same instance.
