@@ -5,6 +5,10 @@ GPU library is checked against; only the tests, ``__graft_entry__.smoke()`` and
 the CPU-baseline leg of ``bench.py`` may import it.  It shares no code with the
 CUDA library: the C source here (``curob_oracle.c``) re-states every formula of
 the paper on its own, and this module only compiles it and marshals arrays.
+
+Parity unpinned: the readings of points the paper leaves silent or garbled
+(listed in ``curob_oracle.c``) and the instance-generation choices are checked
+for self-consistency only; every formula is pinned by the CPU tests.
 """
 from __future__ import annotations
 

@@ -26,6 +26,11 @@
  *   - inside a hybrid, G_i uses its own scale and offset, and "D" inside
  *     G_i is n_i; an empty block (n_i = 0) contributes 0;
  *   - composition weights at x = o_i are the one-hot limit (first such i).
+ * Parity unpinned: these readings, and the instance-generation choices
+ * (Philox keying and counter layout, Fisher-Yates draw, Box-Muller branch,
+ * Gram-Schmidt order), are choices the paper does not fix; they are checked
+ * for self-consistency only.  Every formula itself is pinned by the CPU
+ * tests (closed forms, f(x_opt) = f_opt, invariances, brute-force grids).
  */
 #include "curob_oracle.h"
 
