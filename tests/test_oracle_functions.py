@@ -279,3 +279,38 @@ def test_grid_minimum_two_dimensional(orc, fid):
     if fid <= 1:
         best = X[np.argmin(f)]
         assert np.abs(best - o).max() <= 0.5 + 1e-9
+
+
+def test_composition_weights_far_outside_the_box(orc):
+    """Far from every member optimum each w_i = exp(-d_i^2/(2 D s_i^2))/d_i
+    underflows to 0 in FP64; the oracle then takes the same normalisation in
+    the log domain.  Composition Function 2 (Schwefel, Rastrigin, HGBat, all
+    sigma = 15, lambda = 1, biases 0/100/200) with identity rotations and
+    o's on the first axis, at x = 2000 e_1: the result equals the weights
+    computed here by log-sum-exp from d_i^2, times the members' values."""
+    D = 4
+    comps = orc.generate(30, D, 0)
+    comps[0].o = np.array([-3.0, 0, 0, 0])
+    comps[1].o = np.array([3.0, 0, 0, 0])
+    comps[2].o = np.array([60.0, 60, 60, 60])
+    for c in comps:
+        if c.rotated:
+            c.S = np.arange(D, dtype=np.int32)
+            c.R = [np.eye(n) for n in c.blocks]
+    x = np.array([[2000.0, 0.0, 0.0, 0.0]])
+    sig, lam, bias = 15.0, 1.0, [0.0, 100.0, 200.0]
+    d2 = [float(np.sum((x[0] - c.o) ** 2)) for c in comps]
+    # the direct weights are all 0 in FP64: the fallback is what is pinned
+    assert all(math.exp(-v / (2 * D * sig * sig)) / math.sqrt(v) == 0.0 for v in d2)
+    G = [orc.G("schwefel", 10.0 * (x[0] - comps[0].o)),
+         orc.G("rastrigin", 0.0512 * (x[0] - comps[1].o)),
+         orc.G("hgbat", 0.05 * (x[0] - comps[2].o) - 1.0)]
+    lw = [-0.5 * math.log(v) - v / (2 * D * sig * sig) for v in d2]
+    mx = max(lw)
+    e = [math.exp(v - mx) for v in lw]
+    expect = sum(ei / sum(e) * (lam * g + b) for ei, g, b in zip(e, G, bias)) + FOPT
+    F = orc.evaluate_given(30, D, comps, x)[0]
+    assert math.isfinite(F)
+    assert abs(F - expect) <= 1e-12 * abs(expect), (F, expect)
+    # the closest member (o_2) carries almost all the weight
+    assert e[1] / sum(e) > 0.999
