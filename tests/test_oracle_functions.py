@@ -312,5 +312,5 @@ def test_composition_weights_far_outside_the_box(orc):
     F = orc.evaluate_given(30, D, comps, x)[0]
     assert math.isfinite(F)
     assert abs(F - expect) <= 1e-12 * abs(expect), (F, expect)
-    # the closest member (o_2) carries almost all the weight
-    assert e[1] / sum(e) > 0.999
+    # the closest member (o_3: d^2 = 1940^2 + 3 * 60^2) carries the weight
+    assert e[2] / sum(e) > 0.999
