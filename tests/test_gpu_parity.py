@@ -178,3 +178,34 @@ def test_host_wrappers(orc):
 def _torch():
     import torch
     return torch
+
+
+def test_composition_far_outside_the_box(orc):
+    """Candidates so far from every member optimum that each composition
+    weight underflows in FP64: the library's log-domain normalisation
+    matches the oracle's (FP64 path to 1e-12, FP32 path to 1e-5)."""
+    torch = _torch()
+    D = 4
+    comps = orc.generate(30, D, 0)
+    comps[0].o = np.array([-3.0, 0, 0, 0])
+    comps[1].o = np.array([3.0, 0, 0, 0])
+    comps[2].o = np.array([60.0, 60, 60, 60])
+    for c in comps:
+        if c.rotated:
+            c.S = np.arange(D, dtype=np.int32)
+            c.R = [np.eye(n) for n in c.blocks]
+    cu = gu.ensure(D, 8)
+    try:
+        for k, c in enumerate(comps):
+            cu.curob_set_component(30, k, c.o, c.S, c.R)
+        x = np.array([[2000.0, 0, 0, 0], [-5000.0, 100, 0, 7], [0, 0, 0, 3000.0]])
+        ref = orc.evaluate_given(30, D, comps, x)
+        got = gu.gpu_eval(30, x, torch.float64)
+        assert np.all(np.isfinite(got))
+        assert np.all(gu.rel_err(got, ref) <= 1e-12), (got, ref)
+        x32 = x.astype(np.float32)
+        got32 = gu.gpu_eval(30, x32, torch.float32)
+        ref32 = orc.evaluate_given(30, D, comps, x32.astype(np.float64))
+        assert np.all(gu.rel_err(got32, ref32) <= 1e-5), (got32, ref32)
+    finally:
+        gu.invalidate()
