@@ -34,3 +34,24 @@ def test_clock_summary_without_samples_says_so():
     c.t_start, c.t_end = 1.0, 2.0
     c.lines = [(0.1, _line(2070)), (9.0, "garbled")]
     assert c.summary()["reasons"] == ["unsampled"]
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` (the FP64 oracle on the host cores) prints
+    one JSON line with the benchmark's metric and unit, impl = reference, its
+    CPU baseline and a zero-copy end-to-end figure."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "1"], capture_output=True, text=True,
+                       timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC
+    assert d["unit"] == "evals/s" and d["higher_is_better"] is True and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    e2e = d["e2e"]
+    assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
