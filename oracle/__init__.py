@@ -86,6 +86,15 @@ def lib():
         L.oracle_evaluate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, dp,
                                       ctypes.c_long, dp, ctypes.c_int]
         L.oracle_evaluate.restype = ctypes.c_int
+        L.oracle_component_z.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, ip, dp,
+                                         dp, ctypes.c_int, dp]
+        L.oracle_component_z.restype = ctypes.c_int
+        L.oracle_evaluate_from_z.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
+        L.oracle_evaluate_from_z.restype = ctypes.c_int
+        L.oracle_compose.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
+        L.oracle_compose.restype = ctypes.c_int
+        L.oracle_block_affine.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
+        L.oracle_block_affine.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -185,3 +194,59 @@ def evaluate(fid: int, D: int, seed: int, x, nthreads: int = 1) -> np.ndarray:
     if rc:
         raise ValueError(f"oracle_evaluate({fid},{D}) -> {rc}")
     return out
+
+
+def _packed_R(comp):
+    parts = [r.reshape(-1) for r in comp.R]
+    return np.ascontiguousarray(np.concatenate(parts) if parts else np.zeros(1))
+
+
+def component_z(fid: int, D: int, comps, c: int, x, plain: bool = False) -> np.ndarray:
+    """z of component c (block order) for one candidate x: one fma per term
+    in index order (as the evaluation), or plain=True for rounded products
+    added in index order."""
+    comp = comps[c]
+    xx = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+    o = np.ascontiguousarray(comp.o, dtype=np.float64)
+    S = np.ascontiguousarray(comp.S, dtype=np.int32)
+    z = np.zeros(D)
+    rc = lib().oracle_component_z(fid, D, c, _dp(o), _ip(S), _dp(_packed_R(comp)), _dp(xx),
+                                  int(plain), _dp(z))
+    if rc:
+        raise ValueError(f"oracle_component_z -> {rc}")
+    return z
+
+
+def evaluate_from_z(fid: int, D: int, zs, d2=None) -> float:
+    """f (f_opt included) from every component's z (list of D-vectors) and,
+    for a composition, the squared distances d2[c] = ||x - o_c||^2."""
+    z = np.ascontiguousarray(np.concatenate([np.asarray(v, dtype=np.float64) for v in zs]))
+    dd = np.ascontiguousarray(np.zeros(max(len(zs), 1)) if d2 is None else d2, dtype=np.float64)
+    out = np.zeros(1)
+    rc = lib().oracle_evaluate_from_z(fid, D, _dp(z), _dp(dd), _dp(out))
+    if rc:
+        raise ValueError(f"oracle_evaluate_from_z -> {rc}")
+    return float(out[0])
+
+
+def compose(fid: int, D: int, G, d2) -> float:
+    """A composition's f (f_opt included) from its members' values G_c and
+    squared distances d2_c (Eq. composition, Eq. weight)."""
+    g = np.ascontiguousarray(G, dtype=np.float64)
+    dd = np.ascontiguousarray(d2, dtype=np.float64)
+    out = np.zeros(1)
+    rc = lib().oracle_compose(fid, D, _dp(g), _dp(dd), _dp(out))
+    if rc:
+        raise ValueError(f"oracle_compose -> {rc}")
+    return float(out[0])
+
+
+def block_affine(fid: int, D: int, comp: int = 0):
+    """([s_b], [c_b]) of component comp's blocks: z_b = R_b (s_b y_b) + c_b."""
+    sc = np.zeros(5)
+    of = np.zeros(5)
+    rc = lib().oracle_block_affine(fid, D, comp, _dp(sc), _dp(of))
+    if rc:
+        raise ValueError(f"oracle_block_affine -> {rc}")
+    nb = len(layout(fid, D, comp)[0])
+    return sc[:nb].tolist(), of[:nb].tolist()

@@ -671,62 +671,122 @@ int oracle_generate_component(int fid, int D, uint64_t seed, int comp,
 /* Evaluation.                                                          */
 /* ------------------------------------------------------------------ */
 
-/* One component's value (no f_opt): basic function or hybrid (Eq. hybrid).
- * work must hold 3*D doubles. */
-static double eval_component(const layout_t* L, int D, const double* o,
-                             const int* S, const double* R, const double* x,
-                             double* work) {
+/* z of one component, in block order (General Setup, "z = R(s(x - o)) + c"):
+ * y = x - o; each block takes y at its variables S_b, scaled by the s of its
+ * basic kind, rotated by R_b and offset by the kind's c (a hybrid's block i
+ * by the s and c of its own G_i, Eq. hybrid).  An unrotated component is
+ * z = s y + c.  plain = 0: each dot product takes one fma per term in index
+ * order (the oracle's evaluation); plain = 1: each product is rounded, then
+ * added, in index order.  work holds 2 D doubles. */
+static void component_z(const layout_t* L, int D, const double* o,
+                        const int* S, const double* R, const double* x,
+                        int plain, double* work, double* z) {
   double* y = work;
   double* v = work + D;
-  double* z = work + 2 * D;
   for (int j = 0; j < D; ++j) y[j] = x[j] - o[j];
-
-  if (L->hybrid_fid >= 0) {
-    /* F = sum_i G_i(R_i z^i): block i takes y at S's i-th segment; G_i
-     * applies its own scale before and offset after its rotation. */
-    const fdesc_t* h = &FTAB[L->hybrid_fid];
-    double total = 0.0;
-    int off = 0;
-    long roff = 0;
-    for (int b = 0; b < L->nb; ++b) {
-      int n = L->sizes[b];
-      int k = h->hk[b];
-      for (int c = 0; c < n; ++c) v[c] = KIND_SCALE[k] * y[S[off + c]];
-      const double* Rb = R + roff;
-      for (int r = 0; r < n; ++r) {
-        double acc = 0.0;
-        for (int c = 0; c < n; ++c) acc = fma(Rb[(long)r * n + c], v[c], acc);
-        z[r] = acc + KIND_OFFSET[k];
-      }
-      total += oracle_G(k, z, n);
-      off += n;
-      roff += (long)n * n;
-    }
-    return total;
-  }
-
-  int k = L->gkind;
   if (!L->rotated) {
+    int k = L->gkind;
     for (int j = 0; j < D; ++j) z[j] = KIND_SCALE[k] * y[j] + KIND_OFFSET[k];
-    return oracle_G(k, z, D);
+    return;
   }
-  /* z = R (s (x - o)) + c with R = P^T-free block rotation: z in block
-   * order, block b = R_b (s y_{S_b}). */
+  const fdesc_t* h = (L->hybrid_fid >= 0) ? &FTAB[L->hybrid_fid] : NULL;
   int off = 0;
   long roff = 0;
   for (int b = 0; b < L->nb; ++b) {
     int n = L->sizes[b];
+    int k = h ? h->hk[b] : L->gkind;
     for (int c = 0; c < n; ++c) v[c] = KIND_SCALE[k] * y[S[off + c]];
     const double* Rb = R + roff;
     for (int r = 0; r < n; ++r) {
       double acc = 0.0;
-      for (int c = 0; c < n; ++c) acc = fma(Rb[(long)r * n + c], v[c], acc);
+      if (plain) {
+        for (int c = 0; c < n; ++c) acc += Rb[(long)r * n + c] * v[c];
+      } else {
+        for (int c = 0; c < n; ++c) acc = fma(Rb[(long)r * n + c], v[c], acc);
+      }
       z[off + r] = acc + KIND_OFFSET[k];
     }
     off += n;
     roff += (long)n * n;
   }
-  return oracle_G(k, z, D);
+}
+
+/* One component's value (no f_opt) from its z: the basic function on the
+ * whole of z, or a hybrid's sum of G_i over its blocks in block order, with
+ * "D" inside G_i equal to n_i (Eq. hybrid). */
+static double component_value(const layout_t* L, int D, const double* z) {
+  if (L->hybrid_fid >= 0) {
+    const fdesc_t* h = &FTAB[L->hybrid_fid];
+    double total = 0.0;
+    int off = 0;
+    for (int b = 0; b < L->nb; ++b) {
+      total += oracle_G(h->hk[b], z + off, L->sizes[b]);
+      off += L->sizes[b];
+    }
+    return total;
+  }
+  return oracle_G(L->gkind, z, D);
+}
+
+/* ||x - o||^2 in index order (Eq. weight's d_i^2). */
+static double sq_distance(int D, const double* x, const double* o) {
+  double s = 0.0;
+  for (int j = 0; j < D; ++j) {
+    double t = x[j] - o[j];
+    s += t * t;
+  }
+  return s;
+}
+
+/* Eq. composition with the weights of Eq. weight (no f_opt):
+ * sum_i omega_i (lambda_i G_i + bias_i), omega_i = w_i / sum_j w_j,
+ * w_i = (1 / sqrt(d_i^2)) exp(-d_i^2 / (2 D sigma_i^2)). */
+static double compose_value(const fdesc_t* f, int nc, int D, const double* G,
+                            const double* d2) {
+  int hit = -1;
+  for (int c = 0; c < nc; ++c)
+    if (d2[c] == 0.0 && hit < 0) hit = c;
+  if (hit >= 0) {
+    /* x = x^{opt,i}: omega is one-hot at i (stated limit) */
+    return f->lambda[hit] * G[hit] + f->bias[hit];
+  }
+  double w[5], W = 0.0;
+  for (int c = 0; c < nc; ++c) {
+    w[c] = (1.0 / sqrt(d2[c])) *
+           exp(-d2[c] / (2.0 * (double)D * f->sigma[c] * f->sigma[c]));
+    W += w[c];
+  }
+  double F = 0.0;
+  if (W > 0.0) {
+    for (int c = 0; c < nc; ++c)
+      F += (w[c] / W) * (f->lambda[c] * G[c] + f->bias[c]);
+    return F;
+  }
+  /* every w_i underflowed (far outside the search box): the same
+   * normalisation taken in the log domain */
+  double lw[5], mx = -INFINITY;
+  for (int c = 0; c < nc; ++c) {
+    lw[c] = -0.5 * log(d2[c]) -
+            d2[c] / (2.0 * (double)D * f->sigma[c] * f->sigma[c]);
+    if (lw[c] > mx) mx = lw[c];
+  }
+  double Z = 0.0;
+  for (int c = 0; c < nc; ++c) Z += exp(lw[c] - mx);
+  for (int c = 0; c < nc; ++c)
+    F += (exp(lw[c] - mx) / Z) * (f->lambda[c] * G[c] + f->bias[c]);
+  return F;
+}
+
+static int make_layouts(int fid, int D, layout_t L[5], long roffs[5]) {
+  int nc = oracle_num_components(fid);
+  long rtot = 0;
+  for (int c = 0; c < nc; ++c) {
+    int rc = make_layout(fid, D, c, &L[c]);
+    if (rc) return rc;
+    if (roffs) roffs[c] = rtot;
+    rtot += layout_rsize(&L[c]);
+  }
+  return 0;
 }
 
 int oracle_evaluate_given(int fid, int D, const double* o, const int* S,
@@ -737,13 +797,8 @@ int oracle_evaluate_given(int fid, int D, const double* o, const int* S,
   int nc = oracle_num_components(fid);
   layout_t L[5];
   long roffs[5];
-  long rtot = 0;
-  for (int c = 0; c < nc; ++c) {
-    int rc = make_layout(fid, D, c, &L[c]);
-    if (rc) return rc;
-    roffs[c] = rtot;
-    rtot += layout_rsize(&L[c]);
-  }
+  int rc0 = make_layouts(fid, D, L, roffs);
+  if (rc0) return rc0;
   if (nthreads < 1) nthreads = 1;
   int err = 0;
 
@@ -758,61 +813,76 @@ int oracle_evaluate_given(int fid, int D, const double* o, const int* S,
     for (long n = 0; n < N; ++n) {
       if (!work) continue;
       const double* xn = x + n * (long)D;
+      double* z = work + 2 * D;
       if (f->type != T_COMPOSITION) {
-        out[n] = eval_component(&L[0], D, o, S, R, xn, work) + F_OPT;
+        component_z(&L[0], D, o, S, R, xn, 0, work, z);
+        out[n] = component_value(&L[0], D, z) + F_OPT;
         continue;
       }
-      /* Eq. composition with weights of Eq. weight */
-      double G[5], d2[5], w[5];
-      int hit = -1;
+      double G[5], d2[5];
       for (int c = 0; c < nc; ++c) {
         const double* oc = o + (long)c * D;
-        G[c] = eval_component(&L[c], D, oc, S + (long)c * D, R + roffs[c], xn,
-                              work);
-        double s = 0.0;
-        for (int j = 0; j < D; ++j) {
-          double t = xn[j] - oc[j];
-          s += t * t;
-        }
-        d2[c] = s;
-        if (s == 0.0 && hit < 0) hit = c;
+        component_z(&L[c], D, oc, S + (long)c * D, R + roffs[c], xn, 0, work, z);
+        G[c] = component_value(&L[c], D, z);
+        d2[c] = sq_distance(D, xn, oc);
       }
-      double F;
-      if (hit >= 0) {
-        /* x = x^{opt,i}: omega is one-hot at i (stated limit) */
-        F = f->lambda[hit] * G[hit] + f->bias[hit];
-      } else {
-        double W = 0.0;
-        for (int c = 0; c < nc; ++c) {
-          w[c] = (1.0 / sqrt(d2[c])) *
-                 exp(-d2[c] / (2.0 * (double)D * f->sigma[c] * f->sigma[c]));
-          W += w[c];
-        }
-        if (W > 0.0) {
-          F = 0.0;
-          for (int c = 0; c < nc; ++c)
-            F += (w[c] / W) * (f->lambda[c] * G[c] + f->bias[c]);
-        } else {
-          /* every w_i underflowed (far outside the search box): the same
-           * normalisation taken in the log domain */
-          double lw[5], mx = -INFINITY;
-          for (int c = 0; c < nc; ++c) {
-            lw[c] = -0.5 * log(d2[c]) -
-                    d2[c] / (2.0 * (double)D * f->sigma[c] * f->sigma[c]);
-            if (lw[c] > mx) mx = lw[c];
-          }
-          double Z = 0.0;
-          for (int c = 0; c < nc; ++c) Z += exp(lw[c] - mx);
-          F = 0.0;
-          for (int c = 0; c < nc; ++c)
-            F += (exp(lw[c] - mx) / Z) * (f->lambda[c] * G[c] + f->bias[c]);
-        }
-      }
-      out[n] = F + F_OPT;
+      out[n] = compose_value(f, nc, D, G, d2) + F_OPT;
     }
     free(work);
   }
   return err;
+}
+
+int oracle_component_z(int fid, int D, int comp, const double* o,
+                       const int* S, const double* R, const double* x,
+                       int plain, double* z) {
+  layout_t L;
+  int rc = make_layout(fid, D, comp, &L);
+  if (rc) return rc;
+  double* work = (double*)malloc(sizeof(double) * 2 * (size_t)D);
+  if (!work) return -4;
+  component_z(&L, D, o, S, R, x, plain, work, z);
+  free(work);
+  return 0;
+}
+
+int oracle_block_affine(int fid, int D, int comp, double scale[5],
+                        double offset[5]) {
+  layout_t L;
+  int rc = make_layout(fid, D, comp, &L);
+  if (rc) return rc;
+  const fdesc_t* h = (L.hybrid_fid >= 0) ? &FTAB[L.hybrid_fid] : NULL;
+  for (int b = 0; b < 5; ++b) {
+    int k = (h && b < L.nb) ? h->hk[b] : L.gkind;
+    scale[b] = (b < L.nb) ? KIND_SCALE[k] : 0.0;
+    offset[b] = (b < L.nb) ? KIND_OFFSET[k] : 0.0;
+  }
+  return 0;
+}
+
+int oracle_evaluate_from_z(int fid, int D, const double* z, const double* d2,
+                           double* out) {
+  if (!valid_fid(fid)) return -1;
+  const fdesc_t* f = &FTAB[fid];
+  int nc = oracle_num_components(fid);
+  layout_t L[5];
+  int rc = make_layouts(fid, D, L, NULL);
+  if (rc) return rc;
+  if (f->type != T_COMPOSITION) {
+    *out = component_value(&L[0], D, z) + F_OPT;
+    return 0;
+  }
+  double G[5];
+  for (int c = 0; c < nc; ++c) G[c] = component_value(&L[c], D, z + (long)c * D);
+  *out = compose_value(f, nc, D, G, d2) + F_OPT;
+  return 0;
+}
+
+int oracle_compose(int fid, int D, const double* G, const double* d2,
+                   double* out) {
+  if (!valid_fid(fid) || FTAB[fid].type != T_COMPOSITION) return -1;
+  *out = compose_value(&FTAB[fid], FTAB[fid].nc, D, G, d2) + F_OPT;
+  return 0;
 }
 
 int oracle_evaluate(int fid, int D, uint64_t seed, const double* x, long N,

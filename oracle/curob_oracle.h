@@ -88,6 +88,30 @@ int oracle_evaluate_given(int fid, int D, const double* o, const int* S,
                           const double* R, const double* x, long N,
                           double* out, int nthreads);
 
+/* z of component comp (block order, D values) for one candidate x, with that
+ * component's own o[D], S[D] and packed R: z = R(s (x - o)) + c.  plain = 0:
+ * each dot product one fma per term in index order, as oracle_evaluate_given;
+ * plain = 1: each product rounded, then added. */
+int oracle_component_z(int fid, int D, int comp, const double* o,
+                       const int* S, const double* R, const double* x,
+                       int plain, double* z);
+
+/* The scale s and offset c of each block of component comp (z_b =
+ * R_b (s_b y_b) + c_b; an unrotated component reports its one block). */
+int oracle_block_affine(int fid, int D, int comp, double scale[5],
+                        double offset[5]);
+
+/* f (f_opt included) of one candidate from its components' z (n_comp x D,
+ * block order) and, for a composition, d2[c] = ||x - o_c||^2 (Eq. weight);
+ * d2 is not read otherwise.  The same assembly as oracle_evaluate_given. */
+int oracle_evaluate_from_z(int fid, int D, const double* z, const double* d2,
+                           double* out);
+
+/* A composition's value (f_opt included) from its members' G_c and d2_c
+ * (Eq. composition, Eq. weight).  -1 if fid is not a composition. */
+int oracle_compose(int fid, int D, const double* G, const double* d2,
+                   double* out);
+
 /* Generate the instance from seed and evaluate. */
 int oracle_evaluate(int fid, int D, uint64_t seed, const double* x, long N,
                     double* out, int nthreads);
