@@ -189,6 +189,162 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+# Algorithmic work per variable of each basic function on the FP32 path
+# (Table 1 rows 0..22, the order curob_component_kinds reports): (SFU
+# operations, FP32 ALU instructions, an FMA counting one), the minimum the
+# formula needs; pair kinds count per pair.  Weierstrass: 21 cosines and a
+# phase multiply and an FMA per term; Katsuura: 32 terms of (double, round,
+# |.| FMA) and a power (lg2, ex2); Schaffer F7: two square roots, a power and
+# a sine per pair; the others their transcendentals (one SFU operation each)
+# and a few arithmetic instructions.
+KIND_OPS = [
+    (0, 1), (0, 2), (0, 2), (0, 1), (0, 1), (2, 4), (0, 1), (0, 3),   # sphere .. step
+    (21, 42), (2, 4), (1, 3), (5, 8), (1, 8), (0, 5), (2, 4),          # weierstrass .. schwefel
+    (2, 100), (1, 6), (1, 2), (0, 2), (0, 3), (3, 8),                  # katsuura .. schaffer F6
+]
+# partial sums a kind keeps (FP64 additions per 32 columns in the epilogue)
+KIND_SUMS = [1, 1, 1, 2, 2, 1, 2, 1, 1, 2, 1, 1, 1, 1, 1, 2, 3, 2, 2, 3, 1]
+SMS = 152
+SFU_PER_CLK = 16     # SFU results per clock per SM
+FP32_PER_CLK = 128   # FP32 lanes per clock per SM
+FP64_NOMINAL = 1.25e12  # FP64 FLOP/s of the part (an FMA counting two)
+TF32_OVER_BF16 = 1.1 / 2.25  # dense TF32 / BF16 tensor rate, nominal
+
+
+def _profile_traffic():
+    """DRAM bytes per call of the dominant group from the committed ncu
+    summary, when it was taken of the kernel sources as they are now; else
+    None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic_per_call.txt")
+    if not os.path.exists(path):
+        return None, None
+    h = hashlib.sha256()
+    for f in ("curob_mma.cu", "curob_device.cuh", "curob_tc.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1407_7737_gb300", "csrc", f), "rb").read())
+    want = h.hexdigest()[:16]
+    sha, table = None, {}
+    for ln in open(path):
+        ln = ln.strip()
+        if ln.startswith("kernel_sources_sha256_16:"):
+            sha = ln.split(":", 1)[1].strip()
+        elif ln.startswith("group ") and ":" in ln:
+            k, v = ln[6:].split(":", 1)
+            table[k.strip()] = float(v.split()[0])
+    return (table if sha == want else None), want
+
+
+def roofline(cu, pk, src, modes, launch_ms, launches, args):
+    """Per-function binding roofline and the dominant group's tensor line.
+
+    Per function, the time each unit would need at its peak for the work
+    the function algorithmically requires: tensor (2 sum_b n_b^2 FLOP per
+    candidate and rotated component, at the rate of algorithmic products the
+    member's precision reaches), HBM (4 D + 4 bytes per candidate: x read
+    once, f written), SFU and FP32 ALU (KIND_OPS per variable), FP64 (the
+    partial sums per 32 columns, ||x - o||^2 of composition members per 16
+    columns, the composition's weights); the binding bound is the largest,
+    and frac_of_binding = bound / measured time.  The dominant group (the
+    precision holding most of the step's time) is reported as a tensor line:
+    achieved = its algorithmic FLOP / its CUDA-event time, peak = the rate its
+    members' precisions reach."""
+    bf16 = pk["bf16_tflops"]
+    clk = pk.get("sm_max_mhz", 2070.0) * 1e6
+    mode_peak = {1: bf16 * TF32_OVER_BF16 / 3.0, 2: bf16 / 3.0, 4: bf16 / 10.0,
+                 3: SMS * FP32_PER_CLK * 2 * clk / 1e12 / 6.0}
+    sfu_rate = SMS * SFU_PER_CLK * clk
+    alu_rate = SMS * FP32_PER_CLK * clk
+    f64_rate = FP64_NOMINAL / 2.0
+    hbm = pk["hbm_gbs"] * 1e9
+    flops = np.zeros(NFUN)
+    per_fn = []
+    units = ("tensor", "hbm", "sfu", "alu", "fp64")
+    t_bind = np.zeros(NFUN)
+    t_tensor = np.zeros(NFUN)
+    for f in range(NFUN):
+        t = dict.fromkeys(units, 0.0)
+        ncomp = cu.curob_num_components(f)
+        sfu = alu = f64 = 0.0
+        for c in range(ncomp):
+            sizes, rot = cu.curob_component_layout(f, c)
+            kinds = cu.curob_component_kinds(f, c)
+            if rot:
+                fl = 2.0 * sum(n * n for n in sizes) * N
+                flops[f] += fl
+                t["tensor"] += fl / (mode_peak[cu.curob_query_component_precision(f, c)] * 1e12)
+            for n, k in zip(sizes if rot else [D], kinds):
+                sfu += KIND_OPS[k][0] * n
+                alu += KIND_OPS[k][1] * n
+                f64 += KIND_SUMS[k] * n / 32.0
+            if ncomp > 1:
+                f64 += D / 16.0 + 20.0
+        t["hbm"] = (4.0 * D + 4.0) * N / hbm
+        t["sfu"] = sfu * N / sfu_rate
+        t["alu"] = alu * N / alu_rate
+        t["fp64"] = f64 * N / f64_rate
+        b = max(units, key=lambda u: t[u])
+        t_bind[f] = t[b]
+        t_tensor[f] = t["tensor"]
+        per_fn.append({"fid": f, "ms": round(float(launch_ms[f]), 4),
+                       "bound_ms": {u: round(t[u] * 1e3, 4) for u in units},
+                       "binding": b, "frac_of_binding": round(t[b] * 1e3 / float(launch_ms[f]), 4)})
+    modes_a = np.array(modes)
+    share = {m: launch_ms[modes_a == m].sum() for m in set(modes)}
+    dom = max(share, key=share.get)
+    sel = (modes_a == dom) & (flops > 0)
+    achieved = flops[sel].sum() / (launch_ms[sel].sum() / 1e3) / 1e12
+    peak = flops[sel].sum() / t_tensor[sel].sum() / 1e12
+    names = {1: "mma_eval_kernel<TF32X3> (+ finish_kernel for heavy kinds)",
+             2: "mma_eval_kernel<BF16X3> (+ finish_kernel for heavy kinds)",
+             4: "mma_eval_kernel<EXACT> (+ finish_kernel for heavy kinds)",
+             3: "eval_simt_f32_kernel",
+             5: "mma_eval_kernel<EXACT> + <TF32X3> + finish_kernel (mixed compositions)"}
+    group = {1: "tf32x3", 2: "bf16x3", 4: "exact", 3: "simt", 5: "mixed"}[dom]
+    table, sha = _profile_traffic()
+    traffic = table.get(group) if (table and args.precision == "auto") else None
+    roof = {"bound": "tensor" if dom != 3 else "alu", "kernel": names[dom],
+            "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4),
+            "traffic": traffic, "traffic_unit": "DRAM bytes per function call (ncu)",
+            "traffic_kernel_sources_sha256_16": sha,
+            "algorithmic_bytes_per_call": (4 * D + 4) * N,
+            "peak_source": f"{src} bf16 burst; per algorithmic product: EXACT / 10 BF16 products, "
+                           "TF32X3 x 1.1/2.25 (TF32/BF16 dense, nominal) / 3 TF32 products",
+            "share_of_step": round(share[dom] / launch_ms.sum(), 3),
+            "launches_per_step": int(np.array(launches)[sel].sum()),
+            "frac_of_binding": round(float(t_bind[sel].sum() / (launch_ms[sel].sum() / 1e3)), 4),
+            "binding_units": {u: int(sum(1 for f in np.nonzero(sel)[0]
+                                         if per_fn[f]["binding"] == u)) for u in units},
+            "step_frac_of_binding": round(float(t_bind.sum() / (launch_ms.sum() / 1e3)), 4),
+            "peaks": {"sfu_per_s": sfu_rate, "fp32_alu_per_s": alu_rate, "fp64_fma_per_s": f64_rate,
+                      "hbm_bytes_per_s": hbm, "clock_hz": clk,
+                      "source": "SFU 16 and FP32 128 per clock per SM x 152 SMs x the maximum SM "
+                                "clock of MEASURED_PEAKS; FP64 1.25 TFLOP/s nominal; HBM measured"},
+            "note": "achieved = algorithmic flops (2*sum n_b^2 per candidate and rotated "
+                    "component) / CUDA-event time of those functions' calls"}
+    return roof, per_fn
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model"):
+                v = ln.split(":", 1)[1].strip()
+                if v and not v.isdigit():
+                    return v
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
 def run_curob(args):
     import torch
     from paper_1407_7737_gb300 import binding as cu
@@ -327,8 +483,16 @@ def run_curob(args):
     extra = {}
     fp64 = None
     if rank == 0 and not args.no_extra:
+        # whether the forced precision meets the FP32 tolerance on every
+        # function at this size (GPU parity tests): TF32X3 and BF16X3 do not
+        # on the functions that magnify contraction error, which AUTO routes
+        # to EXACT
+        meets = {"tf32x3": False, "bf16x3": False, "exact": True, "simt": True}
+        forced = {}
         for name, m in (("tf32x3", 1), ("bf16x3", 2), ("exact", 4), ("simt", 3)):
-            extra[name + "_evals_s"] = round(NFUN * N / (timed_pass(m) / 1e3), 1)
+            forced[name] = {"evals_s": round(NFUN * N / (timed_pass(m) / 1e3), 1),
+                            "meets_fp32_tolerance_on_all_functions": meets[name]}
+        extra["forced_precision"] = forced
         # FP64 path on the same workload (FP64 copy of the batches)
         x64 = torch.empty((N, D), dtype=torch.float64, device=dev)
         o64 = torch.empty(N, dtype=torch.float64, device=dev)
@@ -349,79 +513,30 @@ def run_curob(args):
     if rank == 0 and not args.no_extra:
         ragged = ragged_batch(cu, torch, dev, stream, reps=max(3, args.steps))
 
-    # roofline of the dominant kernel group (the precision holding most of the
-    # step).  Algorithmic work: 2 sum_b n_b^2 flops per candidate and rotated
-    # component; each component's peak is the rate of algorithmic products its
-    # precision reaches (TF32X3: 3 TF32 products per product, EXACT: 10 BF16
-    # products).  A MIXED composition runs its members at their own
-    # precisions, so its peak is the members' blend: frac = (time the members
-    # would take at their peaks) / (measured time).
     pk, src = peaks()
-    bf16 = pk["bf16_tflops"]
-    mode_peak = {1: bf16 * (1.1 / 2.25) / 3.0, 2: bf16 / 3.0, 4: bf16 / 10.0,
-                 3: 152 * 128 * 2 * 2.07e9 / 1e12 / 6.0}
-    mode_name = {1: "mma_eval_kernel<TF32X3> (+ finish_kernel for heavy kinds)",
-                 2: "mma_eval_kernel<BF16X3> (+ finish_kernel for heavy kinds)",
-                 4: "mma_eval_kernel<EXACT> (+ finish_kernel for heavy kinds)",
-                 3: "eval_simt_f32_kernel",
-                 5: "mma_eval_kernel<EXACT> + <TF32X3> + finish_kernel (mixed compositions)"}
-    flops = np.zeros(NFUN)
-    t_bound = np.zeros(NFUN)  # seconds at the tensor peaks of the components' precisions
-    for f in range(NFUN):
-        for c in range(cu.curob_num_components(f)):
-            sizes, rot = cu.curob_component_layout(f, c)
-            if not rot:
-                continue
-            fl = 2.0 * sum(n * n for n in sizes) * N
-            flops[f] += fl
-            t_bound[f] += fl / (mode_peak[cu.curob_query_component_precision(f, c)] * 1e12)
-    modes_a = np.array(modes)
-    share = {m: launch_ms[modes_a == m].sum() for m in set(modes)}
-    dom = max(share, key=share.get)
-    sel = (modes_a == dom) & (flops > 0)
-    achieved = flops[sel].sum() / (launch_ms[sel].sum() / 1e3) / 1e12
-    peak = flops[sel].sum() / t_bound[sel].sum() / 1e12
-    # DRAM bytes per function call of each group, measured with ncu (one-pass
-    # dram__bytes_read.sum + dram__bytes_write.sum over the 5 timed steps of
-    # `python bench.py --steps 5 --warmup 3`, this version of the kernels):
-    # a light call reads x once (65.6 MB of input, 4 D + 4 bytes per
-    # candidate); a heavy-kind member adds its z round trip through the
-    # scratch (written by the tensor-core kernel, read by finish_kernel); a
-    # MIXED composition reads x once per precision subset.
-    dram_per_call = {1: 106.2e6, 4: 122.9e6, 5: 324.4e6}
-    traffic = dram_per_call.get(dom) if args.precision == "auto" else None
-    roof = {"bound": "tensor" if dom != 3 else "alu", "kernel": mode_name[dom],
-            "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 4),
-            "traffic": traffic, "traffic_unit": "bytes per function call",
-            "algorithmic_bytes_per_call": (4 * D + 4) * N,
-            "peak_source": f"{src} bf16 burst; per algorithmic product: EXACT / 10 BF16 products, "
-                           "TF32X3 x 1.1/2.25 (TF32/BF16 nominal ratio) / 3 TF32 products",
-            "share_of_step": round(share[dom] / launch_ms.sum(), 3),
-            "launches_per_step": int(np.array(launches)[sel].sum()),
-            "note": "achieved = algorithmic flops (2*sum n_b^2 per candidate and rotated "
-                    "component) / CUDA-event time of those functions' calls"}
-    # per function: time against its tensor bound and the HBM bound of
-    # reading x once (4 D + 4 bytes per candidate)
-    per_fn = []
-    for f in range(NFUN):
-        t_tc = t_bound[f] * 1e3
-        t_hbm = (4.0 * D + 4.0) * N / (pk["hbm_gbs"] * 1e9) * 1e3
-        per_fn.append({"fid": f, "ms": round(float(launch_ms[f]), 4),
-                       "tensor_bound_ms": round(t_tc, 4), "hbm_bound_ms": round(t_hbm, 4),
-                       "frac_of_binding": round(max(t_tc, t_hbm) / float(launch_ms[f]), 4)})
-
+    roof, per_fn = roofline(cu, pk, src, modes, launch_ms, launches, args)
     e2e = None
     if not args.no_e2e:
-        # End to end through the public API: every step copies each call's
-        # inputs from pinned host memory, evaluates (curob_evaluatef) and
-        # reads the values back, each call on its own stream of the S so
-        # that copies overlap other calls' kernels.  The synchronous
-        # host-pointer call (curob_h_evaluatef) is timed beside it.
+        # End to end through the boundary's host-pointer call (the paper's
+        # h_func_evaluatef): every call copies its batch in from pinned host
+        # memory, evaluates and copies the values back (the library overlaps
+        # the copy of one chunk with the kernels of the others); one step is
+        # the 37 calls.  Beside it, the device-pointer API with the copies
+        # issued by the caller over the step's streams, so that copies overlap
+        # other calls' kernels.
         hx = torch.empty((N, D), dtype=torch.float32, pin_memory=True)
         hx.uniform_(-100, 100)
         hout = torch.empty((NFUN, N), dtype=torch.float32, pin_memory=True)
         lanes = side if S > 1 else [stream]
+        for fid in range(NFUN):
+            cu.curob_h_evaluatef(fid, hx, N, hout[fid])
+        reps = max(1, args.steps // 2)
+        barrier(pg)
+        tt = time.perf_counter()
+        for _ in range(reps):
+            for fid in range(NFUN):
+                cu.curob_h_evaluatef(fid, hx, N, hout[fid])
+        el_h = dist_max(pg, (time.perf_counter() - tt) / reps, dev)
 
         def e2e_step():
             for fid in range(NFUN):
@@ -434,23 +549,17 @@ def run_curob(args):
             torch.cuda.synchronize()
 
         e2e_step()
-        reps = max(1, args.steps // 2)
         barrier(pg)
         tt = time.perf_counter()
         for _ in range(reps):
             e2e_step()
         el = dist_max(pg, (time.perf_counter() - tt) / reps, dev)
-        hsync = torch.empty(N, dtype=torch.float32, pin_memory=True)
-        for fid in range(NFUN):
-            cu.curob_h_evaluatef(fid, hx, N, hsync)
-        tt = time.perf_counter()
-        for fid in range(NFUN):
-            cu.curob_h_evaluatef(fid, hx, N, hsync)
-        el_h = time.perf_counter() - tt
-        e2e = {"value": round(NFUN * N * world / el, 1), "unit": "evals/s",
+        e2e = {"value": round(NFUN * N * world / el_h, 1), "unit": "evals/s",
                "h2d_bytes_per_step": NFUN * N * D * 4, "d2h_bytes_per_step": NFUN * N * 4,
-               "api": f"curob_evaluatef on {len(lanes)} stream(s), pinned host copies in and out",
-               "h_evaluatef_evals_s": round(NFUN * N / el_h, 1)}
+               "api": "curob_h_evaluatef (host buffers, pinned), 37 calls per step",
+               "device_api_overlapped_evals_s": round(NFUN * N * world / el, 1),
+               "device_api_overlapped": f"caller's copies + curob_evaluatef on {len(lanes)} "
+                                        "stream(s), copies overlapping other calls' kernels"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -468,7 +577,9 @@ def run_curob(args):
             "metric": METRIC, "value": round(value, 1), "unit": "evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 (tf32x3/bf16x3 rotation, f64 shift)", "data": "synthetic",
+            "dtype": "f32 in/out; rotation on tensor cores as tf32x3 (3 TF32 products) or exact "
+                     "(BF16 integer slices), per function and member (auto); double-float "
+                     "shift; FP64 sums", "data": "synthetic",
             "config": {"workload": f"37 functions x N={N} candidates U[-100,100]^{D}, FP32",
                        "D": D, "N": N, "functions": NFUN, "precision": args.precision,
                        "l2": "37 distinct input batches (2.4 GB) > L2 per step",
@@ -650,25 +761,27 @@ def ragged_batch(cu, torch, dev, stream, reps=5, n_items=64, seed=2024):
 
 def cpu_baseline(sample_n=8, budget_s=25.0):
     """The FP64 oracle on the host's cores: every function on sample_n
-    candidates of the D = 1000 workload (bounded to ~budget_s of CPU work)."""
+    candidates of the D = 1000 workload (bounded to ~budget_s of CPU work),
+    on all cores and on one core; instance setup excluded."""
     import oracle
     from paper_1407_7737_gb300 import inputs
     cores = os.cpu_count() or 1
+    comps = {fid: oracle.generate(fid, D, SEED) for fid in range(NFUN)}  # setup, not timed
     x = inputs.uniform(max(sample_n, cores), D, 77)
     t = time.perf_counter()
-    n_done = 0
     for fid in range(NFUN):
-        oracle.evaluate(fid, D, SEED, x, nthreads=cores)  # includes instance setup
-        n_done += x.shape[0]
-    total = time.perf_counter() - t
-    # setup (generation) is not evaluation: time it alone and subtract
+        oracle.evaluate_given(fid, D, comps[fid], x, nthreads=cores)
+    ev = max(time.perf_counter() - t, 1e-9)
+    x1 = x[:2]
     t = time.perf_counter()
     for fid in range(NFUN):
-        oracle.generate(fid, D, SEED)
-    gen = time.perf_counter() - t
-    ev = max(total - gen, 1e-9)
-    return {"value": round(n_done / ev, 2), "unit": "evals/s", "cores": cores, "kind": "oracle",
-            "sample": f"{x.shape[0]} candidates x 37 functions at D={D} (instance setup excluded)"}
+        oracle.evaluate_given(fid, D, comps[fid], x1, nthreads=1)
+    ev1 = max(time.perf_counter() - t, 1e-9)
+    return {"value": round(NFUN * x.shape[0] / ev, 2), "unit": "evals/s", "cores": cores,
+            "kind": "oracle", "cpu_model": cpu_model(),
+            "one_core_evals_s": round(NFUN * x1.shape[0] / ev1, 2),
+            "sample": f"{x.shape[0]} candidates x 37 functions at D={D} on {cores} threads, "
+                      f"{x1.shape[0]} x 37 on one thread (instance setup excluded)"}
 
 
 def run_reference(args):
@@ -699,7 +812,7 @@ def run_reference(args):
                        "D": D, "N": N, "functions": NFUN,
                        "sample": f"{n} candidates per function per step"},
             "cpu_baseline": {"value": round(value, 2), "unit": "evals/s", "cores": cores,
-                             "kind": "oracle",
+                             "kind": "oracle", "cpu_model": cpu_model(),
                              "sample": f"{n} candidates x 37 functions at D={D} per step"},
             "e2e": {"value": round(value, 2), "unit": "evals/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}

@@ -21,6 +21,10 @@
  *    curob_dispose, like the paper's compile-time DIM (Sec. 1.3).  Calls are
  *    thread-safe with respect to one another; evaluations may overlap on
  *    different streams.
+ *  - The instance lives on the device that was current at curob_initialize.
+ *    Every evaluation must be made with that device current and with x and
+ *    out in its memory (or managed memory); otherwise it returns
+ *    CUROB_ERR_INVALID_ARGUMENT and launches nothing.
  */
 #ifndef CUROB_H
 #define CUROB_H
@@ -112,8 +116,17 @@ curob_status curob_evaluate(int fid, const double* x, int N, double* out, curob_
  * sizes. */
 curob_status curob_evaluatef(int fid, const float* x, int N, float* out, curob_stream_t stream);
 
-/* Sec. 1.3, h_func_evaluate / h_func_evaluatef: host-pointer wrappers.
- * Copy x in, evaluate on the library's own stream, copy out, synchronise. */
+/* Sec. 1.3, h_func_evaluate / h_func_evaluatef: host-pointer wrappers (x:
+ * N x D host array, out: N host values).  The call is cut into up to four
+ * chunks of whole 128-candidate tiles (one chunk below 2048 candidates), each
+ * copied in, evaluated and copied out on its own library stream, so that a
+ * chunk's copy-in overlaps the kernels of the chunks before it; the values
+ * are those of curob_evaluate / curob_evaluatef.  Returns once out is
+ * written (synchronous).  Copies run at full speed from page-locked host
+ * memory; pageable memory works but the copies then stage through the
+ * driver.  The staging buffers are the library's: concurrent host-wrapper
+ * calls from several threads are serialised.  Errors: those of
+ * curob_evaluate / curob_evaluatef. */
 curob_status curob_h_evaluate(int fid, const double* x, int N, double* out);
 curob_status curob_h_evaluatef(int fid, const float* x, int N, float* out);
 
@@ -168,6 +181,17 @@ curob_status curob_num_components(int fid, int* ncomp);
  * Host pointers. */
 curob_status curob_component_layout(int fid, int comp, int* n_blocks, int sizes[5], int* rotated);
 
+/* Basic function of each non-empty block of component comp, in z order
+ * (host pointers): the Table 1 row 0..22 it is taken from (0 Sphere,
+ * 1 Ellipsoid, 2 Elliptic, 3 Discus, 4 Bent Cigar, 5 Different Powers,
+ * 6 Sharp Valley, 7 Step, 8 Weierstrass, 9 Griewank, 10 Rastrigin,
+ * 11 Schaffer F7, 12 expanded Griewank-Rosenbrock, 13 Rosenbrock,
+ * 14 Modified Schwefel, 15 Katsuura, 16 Lunacek bi-Rastrigin, 17 Ackley,
+ * 18 HappyCat, 19 HGBat, 20 expanded Schaffer F6); a hybrid's blocks carry
+ * their G_i (Sec. 5), a composition member its G (Sec. 6).  Unused entries
+ * are -1.  Errors as curob_component_layout. */
+curob_status curob_component_kinds(int fid, int comp, int* n_blocks, int kinds[5]);
+
 /* Copy component comp's instance data to host memory: o[D] (x^{opt,comp}),
  * S[D] (variable indices in block order; block b takes S[off_b..off_b+n_b)),
  * R (each rotation block n_b x n_b row-major, blocks back to back; nothing for
@@ -204,8 +228,11 @@ curob_status curob_get_optimum(int fid, double* xopt);
  * N[i] <= max_concurrency, block widths <= 512 (else UNSUPPORTED).  The
  * first call on a device looks the array's address up.  All calls share the
  * array and each call overwrites it: calls that overlap on the GPU (two
- * streams, two threads) race; order them on one stream.  Asynchronous on
- * `stream`. */
+ * streams, two threads) race; order them on one stream.  The kernel runs
+ * asynchronously on `stream`, but the call copies its work list and argument
+ * blocks from static (pageable) host arrays, so it may block the host until
+ * earlier work on `stream` has finished.  The device current at the call
+ * must be the instance's (else INVALID_ARGUMENT). */
 curob_status curob_evaluatef_multi_noalloc(const int* fids, const float* const* x, const int* N,
                                            float* const* out, int n_items, curob_stream_t stream);
 

@@ -47,6 +47,7 @@ _SIGS = [
     ("curob_get_config", _I, [_P, _P]),
     ("curob_num_components", _I, [_I, _P]),
     ("curob_component_layout", _I, [_I, _I, _P, _P, _P]),
+    ("curob_component_kinds", _I, [_I, _I, _P, _P]),
     ("curob_get_component", _I, [_I, _I, _P, _P, _P]),
     ("curob_set_component", _I, [_I, _I, _P, _P, _P]),
     ("curob_get_optimum", _I, [_I, _P]),
@@ -219,6 +220,14 @@ def curob_component_layout(fid, comp):
     _call("curob_component_layout", fid, comp, ctypes.addressof(nb), ctypes.addressof(sizes),
           ctypes.addressof(rot))
     return [sizes[i] for i in range(nb.value)], bool(rot.value)
+
+
+def curob_component_kinds(fid, comp):
+    """Basic-function kind (Table 1 row 0..22) of each block of a component."""
+    nb = ctypes.c_int()
+    kinds = (ctypes.c_int * 5)()
+    _call("curob_component_kinds", fid, comp, ctypes.addressof(nb), ctypes.addressof(kinds))
+    return [kinds[i] for i in range(nb.value)]
 
 
 def curob_get_component(fid, comp):

@@ -24,8 +24,15 @@ struct State {
   Instance inst;
   void* d_hx = nullptr;   // host-wrapper staging (max_conc x D doubles)
   void* d_hout = nullptr; // (max_conc doubles)
-  cudaStream_t hstream = nullptr;
+  cudaStream_t hstream = nullptr;         // host wrappers: chunk 0's stream
+  cudaStream_t hside[3] = {};             // and the other chunks' streams
 };
+
+// Host wrappers cut a call into up to kHostChunks chunks of whole 128-row
+// tiles, each on its own stream (copy in, evaluate, copy out), so that a
+// chunk's copy-in overlaps the kernels of the chunks before it.
+constexpr int kHostChunks = 4;
+constexpr int kHostMinChunk = 1024;  // candidates: smaller calls stay one chunk
 
 State g;
 
@@ -36,9 +43,47 @@ void free_all() {
   cudaFree(g.d_hx);
   cudaFree(g.d_hout);
   if (g.hstream) cudaStreamDestroy(g.hstream);
+  for (cudaStream_t& s : g.hside) {
+    if (s) cudaStreamDestroy(s);
+    s = nullptr;
+  }
   g.d_hx = g.d_hout = nullptr;
   g.hstream = nullptr;
   g.init = false;
+}
+
+cudaStream_t host_stream(int k) { return k == 0 ? g.hstream : g.hside[k - 1]; }
+
+// Copy in, evaluate (eval(x_dev, n, out_dev, stream) on each chunk), copy
+// out, then wait for every chunk.  T is the element type of x and out.
+template <typename T, typename Eval>
+curob_status host_pipeline(const T* x, int N, T* out, Eval eval) {
+  const int D = g.inst.D;
+  int chunks = std::min(kHostChunks, std::max(1, N / kHostMinChunk));
+  const int per = ((N + chunks - 1) / chunks + 127) / 128 * 128;
+  chunks = (N + per - 1) / per;
+  T* dx = static_cast<T*>(g.d_hx);
+  T* dout = static_cast<T*>(g.d_hout);
+  curob_status rc = CUROB_OK;
+  int issued = 0;
+  for (int k = 0; k < chunks && rc == CUROB_OK; ++k, ++issued) {
+    const size_t r0 = (size_t)k * per;
+    const int n = (int)std::min<size_t>(per, (size_t)N - r0);
+    cudaStream_t st = host_stream(k);
+    if (cudaMemcpyAsync(dx + r0 * D, x + r0 * D, sizeof(T) * (size_t)n * D,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      rc = CUROB_ERR_CUDA;
+      break;
+    }
+    rc = eval(dx + r0 * D, n, dout + r0, st);
+    if (rc == CUROB_OK && cudaMemcpyAsync(out + r0, dout + r0, sizeof(T) * (size_t)n,
+                                          cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      rc = CUROB_ERR_CUDA;
+  }
+  for (int k = 0; k < issued; ++k)  // nothing may still use the staging after return
+    if (cudaStreamSynchronize(host_stream(k)) != cudaSuccess && rc == CUROB_OK)
+      rc = CUROB_ERR_CUDA;
+  return rc;
 }
 
 curob_status check_eval_args(int fid, const void* x, int N, const void* out) {
@@ -65,17 +110,32 @@ int resolve_precision(const Function& F) {
   return mode;
 }
 
+// The instance's tables live on the device curob_initialize ran on: a
+// kernel launched on another device would read them through a pointer that
+// device cannot use and fault, so every evaluation requires that device to
+// be current.
+bool on_instance_device() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return dev == g.device;
+}
+
 }  // namespace
 
 // A kernel given a pointer the GPU cannot reach would fault the context, so
-// evaluations accept device (or managed) memory only.
+// evaluations accept device memory of the instance's device, or managed
+// memory, only.
 bool device_accessible(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && (!g.init || a.device == g.device);
 }
 
 }  // namespace curob
@@ -115,7 +175,10 @@ curob_status curob_initialize(int D, int max_concurrency, uint64_t seed) {
     free_all();
     return CUROB_ERR_OUT_OF_MEMORY;
   }
-  if (cudaStreamCreateWithFlags(&g.hstream, cudaStreamNonBlocking) != cudaSuccess) {
+  bool streams_ok = cudaStreamCreateWithFlags(&g.hstream, cudaStreamNonBlocking) == cudaSuccess;
+  for (cudaStream_t& s : g.hside)
+    streams_ok = streams_ok && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+  if (!streams_ok) {
     free_all();
     return CUROB_ERR_CUDA;
   }
@@ -140,6 +203,7 @@ curob_status curob_dispose(void) {
 curob_status curob_evaluate(int fid, const double* x, int N, double* out, curob_stream_t stream) {
   curob_status rc = check_eval_args(fid, x, N, out);
   if (rc != CUROB_OK || N == 0) return rc;
+  if (!on_instance_device()) return CUROB_ERR_INVALID_ARGUMENT;
   if (!device_accessible(x) || !device_accessible(out)) return CUROB_ERR_INVALID_ARGUMENT;
   cudaError_t e = launch_simt_f64(tables(), g.inst.func[fid], x, N, out, (cudaStream_t)stream);
   return e == cudaSuccess ? CUROB_OK : CUROB_ERR_CUDA;
@@ -148,6 +212,7 @@ curob_status curob_evaluate(int fid, const double* x, int N, double* out, curob_
 curob_status curob_evaluatef(int fid, const float* x, int N, float* out, curob_stream_t stream) {
   curob_status rc = check_eval_args(fid, x, N, out);
   if (rc != CUROB_OK || N == 0) return rc;
+  if (!on_instance_device()) return CUROB_ERR_INVALID_ARGUMENT;
   if (!device_accessible(x) || !device_accessible(out)) return CUROB_ERR_INVALID_ARGUMENT;
   const Function& F = g.inst.func[fid];
   const int mode = resolve_precision(F);
@@ -165,31 +230,26 @@ curob_status curob_evaluatef(int fid, const float* x, int N, float* out, curob_s
 curob_status curob_h_evaluate(int fid, const double* x, int N, double* out) {
   curob_status rc = check_eval_args(fid, x, N, out);
   if (rc != CUROB_OK || N == 0) return rc;
-  const size_t in = sizeof(double) * (size_t)N * g.inst.D, ob = sizeof(double) * (size_t)N;
+  // the staging buffers and the streams are shared: one host call at a time
   std::lock_guard<std::mutex> lk(g.mu);
-  if (cudaMemcpyAsync(g.d_hx, x, in, cudaMemcpyHostToDevice, g.hstream) != cudaSuccess)
-    return CUROB_ERR_CUDA;
-  if (launch_simt_f64(tables(), g.inst.func[fid], (const double*)g.d_hx, N, (double*)g.d_hout,
-                      g.hstream) != cudaSuccess)
-    return CUROB_ERR_CUDA;
-  if (cudaMemcpyAsync(out, g.d_hout, ob, cudaMemcpyDeviceToHost, g.hstream) != cudaSuccess ||
-      cudaStreamSynchronize(g.hstream) != cudaSuccess)
-    return CUROB_ERR_CUDA;
-  return CUROB_OK;
+  if (!on_instance_device()) return CUROB_ERR_INVALID_ARGUMENT;
+  const Function& F = g.inst.func[fid];
+  return host_pipeline<double>(x, N, out, [&](const double* dx, int n, double* dout,
+                                              cudaStream_t st) {
+    return launch_simt_f64(tables(), F, dx, n, dout, st) == cudaSuccess ? CUROB_OK
+                                                                        : CUROB_ERR_CUDA;
+  });
 }
 
 curob_status curob_h_evaluatef(int fid, const float* x, int N, float* out) {
   curob_status rc = check_eval_args(fid, x, N, out);
   if (rc != CUROB_OK || N == 0) return rc;
-  const size_t in = sizeof(float) * (size_t)N * g.inst.D, ob = sizeof(float) * (size_t)N;
-  if (cudaMemcpyAsync(g.d_hx, x, in, cudaMemcpyHostToDevice, g.hstream) != cudaSuccess)
-    return CUROB_ERR_CUDA;
-  rc = curob_evaluatef(fid, (const float*)g.d_hx, N, (float*)g.d_hout, g.hstream);
-  if (rc != CUROB_OK) return rc;
-  if (cudaMemcpyAsync(out, g.d_hout, ob, cudaMemcpyDeviceToHost, g.hstream) != cudaSuccess ||
-      cudaStreamSynchronize(g.hstream) != cudaSuccess)
-    return CUROB_ERR_CUDA;
-  return CUROB_OK;
+  std::lock_guard<std::mutex> lk(g.mu);
+  if (!on_instance_device()) return CUROB_ERR_INVALID_ARGUMENT;
+  return host_pipeline<float>(x, N, out, [&](const float* dx, int n, float* dout,
+                                             cudaStream_t st) {
+    return curob_evaluatef(fid, dx, n, dout, st);
+  });
 }
 
 curob_status curob_set_precision(int mode) {
@@ -302,6 +362,21 @@ curob_status curob_component_layout(int fid, int comp, int* n_blocks, int sizes[
   return CUROB_OK;
 }
 
+curob_status curob_component_kinds(int fid, int comp, int* n_blocks, int kinds[5]) {
+  if (!g.init) return CUROB_ERR_NOT_INITIALIZED;
+  if (fid < 0 || fid >= kNumFunctions) return CUROB_ERR_INVALID_FID;
+  int c = g.inst.find_comp(fid, comp);
+  if (c < 0) return g.inst.func_ok[fid] ? CUROB_ERR_INVALID_ARGUMENT : CUROB_ERR_INVALID_DIM;
+  if (!n_blocks || !kinds) return CUROB_ERR_NULL_POINTER;
+  const CompHost& ch = g.inst.chost[c];
+  int k = 0;
+  for (int i = 0; i < 5; ++i) kinds[i] = -1;
+  for (int id : ch.segs)
+    if (k < 5) kinds[k++] = g.inst.segs[id].kind;
+  *n_blocks = k;
+  return CUROB_OK;
+}
+
 curob_status curob_get_component(int fid, int comp, double* o, int* S, double* R) {
   if (!g.init) return CUROB_ERR_NOT_INITIALIZED;
   if (fid < 0 || fid >= kNumFunctions) return CUROB_ERR_INVALID_FID;
@@ -383,6 +458,9 @@ extern "C" curob_status curob_evaluatef_multi_noalloc(const int* fids, const flo
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices)
     return CUROB_ERR_CUDA;
+  // the argument blocks point at the instance's tables, which live on the
+  // device curob_initialize ran on; another current device would fault
+  if (dev != g.device) return CUROB_ERR_INVALID_ARGUMENT;
   if (!g_noalloc_addr[dev]) {  // first call on this device: look the array up once
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {

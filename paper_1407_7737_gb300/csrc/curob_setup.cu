@@ -72,58 +72,54 @@ __global__ void gauss_kernel(const GaussJob* jobs, uint64_t seed, double* R) {
   }
 }
 
-__device__ inline double block_sum(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < nw; ++i) s += red[i];
-  return s;
-}
-
-// Gram-Schmidt over the rows of each block, row r against rows 0..r-1, in the
-// classical form applied twice (each pass: all projections, then one update),
-// then normalised.  One CTA per block; v and the projections live in shared
-// memory (2 n doubles).
-__global__ void gram_schmidt_kernel(const GaussJob* jobs, double* Rall, int* status) {
+// Gram-Schmidt over the rows of each block (General Setup: the Gaussian
+// matrix orthonormalised), modified form with a full second pass: row r is
+// reduced against rows 0..r-1 one at a time, twice, then normalised.  Every
+// dot product and the norm are summed sequentially in index order, each
+// product rounded before it is added (this file is compiled without FMA
+// contraction), so the rows are the same function of the Gaussian entries
+// whatever the launch shape.  One warp per block: the lanes form the products
+// and apply the updates, lane 0 adds the products in order.  Sequential by
+// nature (O(n^3) dependent additions per block); setup only.
+__global__ void __launch_bounds__(32) gram_schmidt_kernel(const GaussJob* jobs, double* Rall,
+                                                          int* status) {
   extern __shared__ double sm[];
   const GaussJob J = jobs[blockIdx.x];
   const int n = J.n;
   double* R = Rall + J.r_off;
-  double* v = sm;
-  double* d = sm + n;
-  __shared__ double red[32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  for (int r = 0; r < n; ++r) {
-    for (int c = tid; c < n; c += blockDim.x) v[c] = R[(long long)r * n + c];
-    __syncthreads();
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int q = warp; q < r; q += nw) {
-        const double* e = R + (long long)q * n;
-        double s = 0.0;
-        for (int c = lane; c < n; c += 32) s = fma(e[c], v[c], s);
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) d[q] = s;
-      }
-      __syncthreads();
-      for (int c = tid; c < n; c += blockDim.x) {
-        double s = v[c];
-        for (int q = 0; q < r; ++q) s = fma(-d[q], R[(long long)q * n + c], s);
-        v[c] = s;
-      }
-      __syncthreads();
+  double* v = sm;      // the row being orthonormalised
+  double* p = sm + n;  // products of the current dot product
+  const int lane = threadIdx.x;
+  // sum_c p[c] in index order, starting from 0 (lane 0), sent to every lane
+  auto ordered_sum = [&]() -> double {
+    __syncwarp();
+    double d = 0.0;
+    if (lane == 0) {
+#pragma unroll 8
+      for (int c = 0; c < n; ++c) d = d + p[c];
     }
-    double part = 0.0;
-    for (int c = tid; c < n; c += blockDim.x) part = fma(v[c], v[c], part);
-    double nrm = sqrt(block_sum(part, red));
+    d = __shfl_sync(0xffffffffu, d, 0);
+    __syncwarp();
+    return d;
+  };
+  for (int r = 0; r < n; ++r) {
+    for (int c = lane; c < n; c += 32) v[c] = R[(long long)r * n + c];
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int q = 0; q < r; ++q) {
+        const double* e = R + (long long)q * n;
+        for (int c = lane; c < n; c += 32) p[c] = v[c] * e[c];
+        const double d = ordered_sum();
+        for (int c = lane; c < n; c += 32) v[c] = v[c] - d * e[c];
+      }
+    }
+    for (int c = lane; c < n; c += 32) p[c] = v[c] * v[c];
+    double nrm = sqrt(ordered_sum());
     if (!(nrm > 1e-10)) {  // a degenerate Gaussian draw (probability zero)
-      if (tid == 0) atomicExch(status, DEV_BAD_ARG);
+      if (lane == 0) atomicExch(status, DEV_BAD_ARG);
       nrm = 1.0;
     }
-    for (int c = tid; c < n; c += blockDim.x) R[(long long)r * n + c] = v[c] / nrm;
-    __syncthreads();
+    for (int c = lane; c < n; c += 32) R[(long long)r * n + c] = v[c] / nrm;
+    __syncwarp();  // row r is read back by every lane for the next rows
   }
 }
 
@@ -187,7 +183,7 @@ cudaError_t launch_gauss_gs(const GaussJob* d_jobs, int njobs, int max_n, uint64
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  gram_schmidt_kernel<<<njobs, 512, smem, st>>>(d_jobs, R, status);
+  gram_schmidt_kernel<<<njobs, 32, smem, st>>>(d_jobs, R, status);
   return cudaGetLastError();
 }
 

@@ -26,10 +26,12 @@ def _gpu():
 @pytest.mark.parametrize("D", [10, 31, 100, 1000])
 def test_instance_generation_matches_oracle(orc, D):
     """o and the permutation bit for bit; rotations orthogonal to 1e-13 and
-    equal to the oracle's up to Gram-Schmidt rounding."""
+    equal to the oracle's to 1e-13 (both run modified Gram-Schmidt twice with
+    the same operation order; the Gaussian entries may differ by an ulp where
+    the two libm's log and cos round differently)."""
     cu = gu.ensure(D, 64)
-    fids = ALL if D < 1000 else [0, 8, 16, 24, 27, 29, 36]
-    for fid in fids:
+    worst = 0.0
+    for fid in ALL:
         ref = orc.generate(fid, D, 0)
         for c, rc in enumerate(ref):
             o, S, R = cu.curob_get_component(fid, c)
@@ -39,7 +41,10 @@ def test_instance_generation_matches_oracle(orc, D):
             for Rg, Ro in zip(R, rc.R):
                 n = Rg.shape[0]
                 assert np.abs(Rg @ Rg.T - np.eye(n)).max() <= 1e-13
-                assert np.abs(Rg - Ro).max() <= 1e-11, (fid, c, np.abs(Rg - Ro).max())
+                d = np.abs(Rg - Ro).max()
+                worst = max(worst, d)
+                assert d <= 1e-13, (fid, c, d)
+    _report(f"instance_D{D}.json", {"max_abs_R_difference": worst})
 
 
 # ------------------------------------------------------------------ FP64 path
@@ -55,6 +60,42 @@ def test_fp64_parity_generated_instance(orc, D, N):
         err = gu.rel_err(got, ref)
         worst[fid] = err.max()
     bad = {f: e for f, e in worst.items() if not e <= 1e-12}
+    assert not bad, bad
+
+
+def test_fp64_parity_generated_instance_full_size(orc):
+    """D = 1000, N = 16384 on the library's own instance: every function
+    against the oracle evaluated on that instance's data (read back through
+    curob_get_component), on sampled rows, and against f from correctly
+    rounded z (oracle.exact, no rounding order shared with either side) on a
+    few of them.  Beside it, the difference to the oracle on its own
+    generated instance is recorded per function: the two instances' R differ
+    by the ulps of the Gaussian draws, which functions with large z
+    sensitivity (Weierstrass's 3^k phases) magnify."""
+    from oracle import exact
+    D, N = 1000, 16384
+    cu = gu.ensure(D, N)
+    rows = np.unique(np.r_[0, 1, N - 1, np.random.default_rng(11).integers(0, N, 61)])
+    xrows = rows[:3]
+    report, bad = {}, {}
+    for fid in ALL:
+        comps = _library_instance(cu, orc, fid, D)
+        o = comps[0].o
+        x = inputs.mixed(N, D, 500 + fid, center=o, frac_near=0.1, sigma=1e-3)
+        got = gu.gpu_eval(fid, x, _torch().float64)
+        ref = orc.evaluate_given(fid, D, comps, x[rows], nthreads=16)
+        err = gu.rel_err(got[rows], ref)
+        xr = np.r_[rows[:2], [int(np.argmin(np.abs(x - o[None, :]).max(axis=1)))]]
+        ex = exact.evaluate(fid, D, comps, x[xr])
+        err_x = gu.rel_err(got[xr], ex)
+        own = orc.evaluate(fid, D, 0, x[rows], nthreads=16)
+        err_own = gu.rel_err(got[rows], own)
+        report[fid] = {"vs_oracle_on_library_instance": float(err.max()),
+                       "vs_correctly_rounded_z": float(err_x.max()),
+                       "vs_oracle_own_instance": float(err_own.max())}
+        if not (err.max() <= 1e-12 and err_x.max() <= 1e-12):
+            bad[fid] = report[fid]
+    _report("fp64_generated_D1000.json", report)
     assert not bad, bad
 
 
@@ -178,6 +219,58 @@ def test_host_wrappers(orc):
 def _torch():
     import torch
     return torch
+
+
+def _library_instance(cu, orc, fid, D):
+    """The library's instance of fid as oracle Components (o, S, R read back)."""
+    comps = []
+    for c in range(cu.curob_num_components(fid)):
+        sizes, rot = cu.curob_component_layout(fid, c)
+        o, S, R = cu.curob_get_component(fid, c)
+        comps.append(orc.Component(o=np.asarray(o), S=np.asarray(S, dtype=np.int32),
+                                   blocks=list(sizes) if rot else [D], R=list(R) if rot else [],
+                                   rotated=bool(rot)))
+    return comps
+
+
+def _report(name, rep):
+    import json
+    import os
+    out = os.environ.get("CUROB_TEST_REPORTS")
+    if out:
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, name), "w") as f:
+            json.dump(rep, f, indent=1)
+
+
+def test_host_wrappers_two_threads(orc):
+    """Two host threads call curob_h_evaluatef at once with different inputs
+    and different functions; each gets its own values (the wrappers share the
+    library's staging buffers, so the calls are serialised)."""
+    import threading
+    cu = gu.ensure(30, 512)
+    xs = [inputs.uniform(512, 30, 40 + k).astype(np.float32) for k in range(2)]
+    fids = (11, 21)
+    outs = [np.zeros(512, dtype=np.float32) for _ in range(2)]
+    errs = []
+
+    def work(k):
+        try:
+            for _ in range(20):
+                cu.curob_h_evaluatef(fids[k], xs[k], 512, outs[k])
+        except Exception as e:  # reported below
+            errs.append(e)
+
+    th = [threading.Thread(target=work, args=(k,)) for k in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errs, errs
+    for k in range(2):
+        ok, worst, excused, raw = gu.fp32_check(orc, fids[k], 30, 0, xs[k],
+                                                outs[k].astype(np.float64))
+        assert ok, (k, raw)
 
 
 def test_composition_far_outside_the_box(orc):

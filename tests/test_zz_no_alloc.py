@@ -5,7 +5,8 @@ optimizer that reserves its whole GPU budget at start-up, a plugin whose host
 framework owns every device allocation).  This entry point keeps its scratch
 in a static device array; here its results are checked, through the C ABI,
 against the ordinary curob_evaluatef on two calls in a row with different
-work, so the second call cannot lean on what the first left in the array.
+work, so the second call cannot lean on what the first left in the array,
+and against the FP64 oracle directly.
 """
 import numpy as np
 import pytest
@@ -65,7 +66,7 @@ def test_noalloc_matches_evaluatef_twice(orc, torch_cuda):
         fused = [cu.curob_query_launches(fid, n) == 1 for fid, n in zip(fids, Ns)]
         cu.curob_set_precision(cu.PRECISION_AUTO)
         assert not all(fused) and any(fused)  # both kinds of item are covered
-        for fid, o, a, e, one in zip(fids, outs, auto, exact, fused):
+        for fid, x, o, a, e, one in zip(fids, xs, outs, auto, exact, fused):
             got = o.cpu().numpy().astype(np.float64)
             fs = gu.f_scale(orc, fid, D, 0)
             for ref_t in (a, e):
@@ -74,6 +75,9 @@ def test_noalloc_matches_evaluatef_twice(orc, torch_cuda):
                 assert ok.all(), (k, fid, float((np.abs(got - ref) / tol).max()))
             if one:  # EXACT in one launch: the same tile arithmetic, bit for bit
                 assert torch.equal(o, e), (k, fid)
+            # and directly against the FP64 oracle at the FP32 inputs
+            ok, worst, excused, raw = gu.fp32_check(orc, fid, D, 0, x.cpu().numpy(), got)
+            assert ok, (k, fid, raw)
 
 
 def test_noalloc_limits(torch_cuda):
