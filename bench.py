@@ -571,6 +571,12 @@ def run_curob(args):
         surrogate = surrogate_bench(cu, torch, dev, stream, args)
         cu.curob_initialize(D, N, SEED)
 
+    small = None
+    if rank == 0 and not args.no_extra:
+        cu.curob_dispose()
+        small = small_batch_latency(cu, torch, stream)
+        cu.curob_initialize(D, N, SEED)
+
     gpu_launches = int(sum(launches)) * args.steps
     if rank == 0:
         line = {
@@ -597,12 +603,55 @@ def run_curob(args):
                                    5: "mixed"}[m] for m in modes],
             "per_function_launches": launches,
             "roofline": roof, "roofline_per_function": per_fn, "cpu_baseline": cpu, "e2e": e2e, "ragged_batch": ragged,
-            "surrogate": surrogate, "clocks": clk.summary(), "gpu_launches": gpu_launches,
+            "surrogate": surrogate, "small_batch": small,
+            "clocks": clk.summary(), "gpu_launches": gpu_launches,
         }
         print(json.dumps(line))
     cu.curob_dispose()
     if pg is not None:
         pg.destroy_process_group()
+
+
+def small_batch_latency(cu, torch, stream, runs=200, n=50):
+    """The paper's timing setting (Sec. 2): N = 50 candidates per call, every
+    function at D = 10, 32, 64, 96, FP32 (curob_evaluatef, AUTO) and FP64
+    (curob_evaluate), each call repeated `runs` times back to back on one
+    stream (CUDA events); mean microseconds per call over the functions."""
+    from paper_1407_7737_gb300 import inputs
+    per_d = {}
+    for d in (10, 32, 64, 96):
+        cu.curob_initialize(d, n, SEED)
+        x64 = torch.from_numpy(inputs.uniform(n, d, 900 + d)).cuda()
+        x32 = x64.float()
+        o64 = torch.empty(n, dtype=torch.float64, device="cuda")
+        o32 = torch.empty(n, dtype=torch.float32, device="cuda")
+        t32, t64, nsmall = [], [], 0
+        for fid in range(NFUN):
+            try:
+                cu.curob_query_precision(fid)
+            except cu.CurobError:
+                continue  # not defined at this D
+            nsmall += int(cu.curob_query_small(fid, n))
+            for call, xx, oo, acc in ((cu.curob_evaluatef, x32, o32, t32),
+                                      (cu.curob_evaluate, x64, o64, t64)):
+                for _ in range(5):
+                    call(fid, xx, n, oo, stream)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(runs):
+                    call(fid, xx, n, oo, stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                acc.append(a.elapsed_time(b) * 1e3 / runs)
+        cu.curob_get_device_status(stream)
+        cu.curob_dispose()
+        per_d[str(d)] = {"functions": len(t32), "small_kernel_functions": nsmall,
+                         "f32_us_per_call_mean": round(float(np.mean(t32)), 2),
+                         "f32_us_per_call_max": round(float(np.max(t32)), 2),
+                         "f64_us_per_call_mean": round(float(np.mean(t64)), 2),
+                         "f64_us_per_call_max": round(float(np.max(t64)), 2)}
+    return {"N": n, "runs": runs, "per_D": per_d}
 
 
 def _rank_corr(torch, a, b):

@@ -133,6 +133,22 @@ curob_status curob_h_evaluatef(int fid, const float* x, int N, float* out);
 /* Select the precision of curob_evaluatef (see curob_precision). */
 curob_status curob_set_precision(int mode);
 
+/* Small populations (the paper's timing setting, Sec. 2: 50 candidates per
+ * call).  A call with N <= max_n candidates -- curob_evaluate, and
+ * curob_evaluatef under CUROB_PRECISION_AUTO -- runs on the small-population
+ * kernels when every block of the function is at most 128 wide: one warp per
+ * candidate and component, one CTA per candidate.  Their arithmetic is that
+ * of the FP64 path (curob_evaluate) and of the compensated CUDA-core FP32
+ * path (curob_evaluatef, CUROB_PRECISION_SIMT).  max_n = 0 turns them off;
+ * the default is 512, and curob_initialize restores it.  Errors:
+ * INVALID_ARGUMENT for max_n < 0. */
+curob_status curob_set_small_batch(int max_n);
+
+/* *small = 1 when a call of fid on N candidates takes the small-population
+ * kernels (see curob_set_small_batch), else 0.  Errors: NOT_INITIALIZED,
+ * INVALID_FID, INVALID_DIM, NULL_POINTER, INVALID_ARGUMENT (N < 0). */
+curob_status curob_query_small(int fid, int N, int* small);
+
 /* The precision curob_evaluatef will use for fid under the current setting
  * (AUTO resolved): CUROB_PRECISION_TF32X3, _BF16X3, _EXACT, _MIXED or _SIMT.
  * Errors: NOT_INITIALIZED, INVALID_FID, INVALID_DIM, NULL_POINTER,

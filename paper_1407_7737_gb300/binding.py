@@ -38,6 +38,8 @@ _SIGS = [
     ("curob_h_evaluate", _I, [_I, _P, _I, _P]),
     ("curob_h_evaluatef", _I, [_I, _P, _I, _P]),
     ("curob_set_precision", _I, [_I]),
+    ("curob_set_small_batch", _I, [_I]),
+    ("curob_query_small", _I, [_I, _I, _P]),
     ("curob_query_precision", _I, [_I, _P]),
     ("curob_query_component_precision", _I, [_I, _I, _P]),
     ("curob_query_launches", _I, [_I, _I, _P]),
@@ -169,6 +171,16 @@ def curob_h_evaluatef(fid, x, N, out, check=True):
 
 def curob_set_precision(mode, check=True):
     return _call("curob_set_precision", mode, check=check)
+
+
+def curob_set_small_batch(max_n, check=True):
+    return _call("curob_set_small_batch", max_n, check=check)
+
+
+def curob_query_small(fid, N):
+    v = ctypes.c_int()
+    _call("curob_query_small", fid, N, ctypes.addressof(v))
+    return bool(v.value)
 
 
 def curob_query_precision(fid):

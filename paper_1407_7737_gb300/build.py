@@ -21,9 +21,11 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC, "-
 EXTRA = {
     "curob_simt64.cu": ["-fmad=false"],
     "curob_setup.cu": ["-fmad=false"],
+    "curob_small64.cu": ["-fmad=false"],
 }
 SOURCES = ["curob_api.cu", "curob_instance.cu", "curob_setup.cu", "curob_simt64.cu",
-           "curob_simt32.cu", "curob_mma.cu", "curob_batch.cu", "curob_mlp.cu"]
+           "curob_simt32.cu", "curob_small64.cu", "curob_small32.cu", "curob_mma.cu",
+           "curob_batch.cu", "curob_mlp.cu"]
 
 
 def _deps():

@@ -15,12 +15,18 @@
 namespace curob {
 namespace {
 
+// Default population limit of the small-population kernels (one warp per
+// candidate and component): below it a call is latency-bound and they finish
+// first; above it the batched kernels' throughput wins.
+constexpr int kSmallBatchDefault = 512;
+
 struct State {
   std::mutex mu;
   bool init = false;
   int max_conc = 0;
   int device = 0;
   int precision = CUROB_PRECISION_AUTO;
+  int small_batch = kSmallBatchDefault;  // calls with N <= this take the small kernels
   Instance inst;
   void* d_hx = nullptr;   // host-wrapper staging (max_conc x D doubles)
   void* d_hout = nullptr; // (max_conc doubles)
@@ -110,6 +116,12 @@ int resolve_precision(const Function& F) {
   return mode;
 }
 
+// A call of N candidates takes the small-population kernels (FP64, and the
+// FP32 path under AUTO) when N is within the limit and every block fits them.
+bool use_small(const Function& F, int N) {
+  return N <= g.small_batch && small_supports(F, g.inst.D);
+}
+
 // The instance's tables live on the device curob_initialize ran on: a
 // kernel launched on another device would read them through a pointer that
 // device cannot use and fault, so every evaluation requires that device to
@@ -188,6 +200,7 @@ curob_status curob_initialize(int D, int max_concurrency, uint64_t seed) {
     return rc;
   }
   g.precision = CUROB_PRECISION_AUTO;
+  g.small_batch = kSmallBatchDefault;
   g.init = true;
   return CUROB_OK;
 }
@@ -205,7 +218,10 @@ curob_status curob_evaluate(int fid, const double* x, int N, double* out, curob_
   if (rc != CUROB_OK || N == 0) return rc;
   if (!on_instance_device()) return CUROB_ERR_INVALID_ARGUMENT;
   if (!device_accessible(x) || !device_accessible(out)) return CUROB_ERR_INVALID_ARGUMENT;
-  cudaError_t e = launch_simt_f64(tables(), g.inst.func[fid], x, N, out, (cudaStream_t)stream);
+  const Function& F = g.inst.func[fid];
+  cudaError_t e = use_small(F, N)
+                      ? launch_small_f64(tables(), F, x, N, out, (cudaStream_t)stream)
+                      : launch_simt_f64(tables(), F, x, N, out, (cudaStream_t)stream);
   return e == cudaSuccess ? CUROB_OK : CUROB_ERR_CUDA;
 }
 
@@ -218,7 +234,9 @@ curob_status curob_evaluatef(int fid, const float* x, int N, float* out, curob_s
   const int mode = resolve_precision(F);
   if (mode < 0) return CUROB_ERR_UNSUPPORTED;
   cudaError_t e;
-  if (mode == CUROB_PRECISION_SIMT)
+  if (g.precision == CUROB_PRECISION_AUTO && use_small(F, N))
+    e = launch_small_f32(tables(), F, x, N, out, (cudaStream_t)stream);
+  else if (mode == CUROB_PRECISION_SIMT)
     e = launch_simt_f32(tables(), F, x, N, out, (cudaStream_t)stream);
   else if (mode == CUROB_PRECISION_MIXED)
     e = launch_mma_mixed(g.inst.mma, tables(), F, x, N, out, (cudaStream_t)stream);
@@ -236,8 +254,9 @@ curob_status curob_h_evaluate(int fid, const double* x, int N, double* out) {
   const Function& F = g.inst.func[fid];
   return host_pipeline<double>(x, N, out, [&](const double* dx, int n, double* dout,
                                               cudaStream_t st) {
-    return launch_simt_f64(tables(), F, dx, n, dout, st) == cudaSuccess ? CUROB_OK
-                                                                        : CUROB_ERR_CUDA;
+    const cudaError_t e = use_small(F, n) ? launch_small_f64(tables(), F, dx, n, dout, st)
+                                          : launch_simt_f64(tables(), F, dx, n, dout, st);
+    return e == cudaSuccess ? CUROB_OK : CUROB_ERR_CUDA;
   });
 }
 
@@ -256,6 +275,22 @@ curob_status curob_set_precision(int mode) {
   if (mode < CUROB_PRECISION_AUTO || mode > CUROB_PRECISION_EXACT)
     return CUROB_ERR_INVALID_ARGUMENT;
   g.precision = mode;
+  return CUROB_OK;
+}
+
+curob_status curob_set_small_batch(int max_n) {
+  if (max_n < 0) return CUROB_ERR_INVALID_ARGUMENT;
+  g.small_batch = max_n;
+  return CUROB_OK;
+}
+
+curob_status curob_query_small(int fid, int N, int* small) {
+  if (!g.init) return CUROB_ERR_NOT_INITIALIZED;
+  if (fid < 0 || fid >= kNumFunctions) return CUROB_ERR_INVALID_FID;
+  if (!g.inst.func_ok[fid]) return CUROB_ERR_INVALID_DIM;
+  if (!small) return CUROB_ERR_NULL_POINTER;
+  if (N < 0) return CUROB_ERR_INVALID_ARGUMENT;
+  *small = (N > 0 && use_small(g.inst.func[fid], N)) ? 1 : 0;
   return CUROB_OK;
 }
 
@@ -290,6 +325,7 @@ curob_status curob_query_launches(int fid, int N, int* launches) {
   if (N < 0) return CUROB_ERR_INVALID_ARGUMENT;
   if (N == 0) *launches = 0;
   else if (m == CUROB_PRECISION_SIMT) *launches = 1;
+  else if (g.precision == CUROB_PRECISION_AUTO && use_small(g.inst.func[fid], N)) *launches = 1;
   else *launches = mma_launch_count(g.inst.func[fid], m, N);
   return CUROB_OK;
 }

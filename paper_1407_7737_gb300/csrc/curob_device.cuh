@@ -66,6 +66,8 @@ struct Function {
                       // Katsuura (2^j phases)
   int sens_mask;      // bit c: component c has such a kind
   int hcols;          // variables of the function's heavy-kind blocks (kind_is_heavy)
+  int nseg;           // segments of all its components (consecutive in the table)
+  int nweier;         // of them, Weierstrass blocks
 };
 
 // Device view of an initialised instance.

@@ -137,6 +137,8 @@ void Instance::build_tables() {
     F.sensitive = 0;
     F.sens_mask = 0;
     F.hcols = 0;
+    F.nseg = 0;
+    F.nweier = 0;
     for (int c = 0; c < ci.n; ++c) {
       const Member& m = ci.m[c];
       CompHost ch;
@@ -191,6 +193,8 @@ void Instance::build_tables() {
           F.hcols += s.n;
         }
         F.max_n = std::max(F.max_n, s.n);
+        F.nseg += 1;
+        F.nweier += s.kind == K_WEIERSTRASS ? 1 : 0;
         if (kind_is_sensitive(s.kind)) {
           F.sensitive = 1;
           F.sens_mask |= 1 << c;

@@ -52,4 +52,13 @@ cudaError_t launch_simt_f64(const Tables& tb, const Function& F, const double* x
 cudaError_t launch_simt_f32(const Tables& tb, const Function& F, const float* x, int N,
                             float* out, cudaStream_t st);
 
+// curob_small64.cu / curob_small32.cu: one CTA per candidate and one warp
+// per block, for small populations; blocks up to 128 wide, at most 16 blocks
+// per function, the CTA's tables within 160 KB of shared memory.
+bool small_supports(const Function& F, int D);
+cudaError_t launch_small_f64(const Tables& tb, const Function& F, const double* x, int N,
+                             double* out, cudaStream_t st);
+cudaError_t launch_small_f32(const Tables& tb, const Function& F, const float* x, int N,
+                             float* out, cudaStream_t st);
+
 }  // namespace curob

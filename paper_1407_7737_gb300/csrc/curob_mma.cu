@@ -156,6 +156,9 @@ struct MmaArgs {
   int acc_ovl;
 };
 
+// The allocation-free entry point keeps up to 64 argument blocks in 32 KB.
+static_assert(sizeof(MmaArgs) <= 512, "MmaArgs outgrew the allocation-free argument area");
+
 // Floats reserved per block for each precision's image (the TF32 size; BF16
 // needs half).  A block's images: [TF32][BF16][EXACT].
 __host__ __device__ inline long long image_floats(int npad) { return 2LL * npad * npad; }

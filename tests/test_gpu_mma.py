@@ -101,17 +101,22 @@ def test_exact_precision_every_function(orc, D, N):
 
 
 def test_ragged_tails(orc):
-    """N not a multiple of the 128-row tile, single candidates."""
+    """N not a multiple of the 128-row tile, single candidates (the
+    small-population kernels turned off, so the tensor-core kernel runs)."""
     import torch
     D = 96
-    for N in (1, 127, 129, 300):
-        gu.ensure(D, 512)
-        for fid in (0, 8, 16, 29, 35):
-            o = orc.generate(fid, D, 0)[0].o
-            x32 = inputs.mixed(N, D, N, center=o, frac_near=0.2, sigma=1e-3).astype(np.float32)
-            got = gu.gpu_eval(fid, x32, torch.float32)
-            ok, *_ = gu.fp32_check(orc, fid, D, 0, x32, got)
-            assert ok, (N, fid)
+    cu = gu.ensure(D, 512)
+    cu.curob_set_small_batch(0)
+    try:
+        for N in (1, 127, 129, 300):
+            for fid in (0, 8, 16, 29, 35):
+                o = orc.generate(fid, D, 0)[0].o
+                x32 = inputs.mixed(N, D, N, center=o, frac_near=0.2, sigma=1e-3).astype(np.float32)
+                got = gu.gpu_eval(fid, x32, torch.float32)
+                ok, *_ = gu.fp32_check(orc, fid, D, 0, x32, got)
+                assert ok, (N, fid)
+    finally:
+        cu.curob_set_small_batch(512)
 
 
 def test_mixed_compositions_choose_member_precisions():
@@ -145,6 +150,7 @@ def test_launch_counts_follow_the_split():
     a composition mixes precisions."""
     cu = gu.ensure(100, 256)
     cu.curob_set_precision(cu.PRECISION_AUTO)
+    cu.curob_set_small_batch(0)  # the batched kernels at every N
     assert cu.curob_query_launches(0, 256) == 1    # Sphere, TF32X3
     assert cu.curob_query_launches(3, 256) == 1    # Discus, EXACT, light
     assert cu.curob_query_launches(8, 256) == 2    # Weierstrass: heavy
@@ -159,6 +165,8 @@ def test_launch_counts_follow_the_split():
         cu.curob_set_precision(cu.PRECISION_AUTO)
     with pytest.raises(cu.CurobError):
         cu.curob_query_launches(8, -1)
+    cu.curob_set_small_batch(512)
+    assert cu.curob_query_launches(32, 256) == 1   # small population: one kernel
 
 
 def test_heavy_scratch_slices(orc):

@@ -154,17 +154,23 @@ def test_fp32_simt_parity(orc, D, N):
 
 
 # ------------------------------------------------------------ edges / errors
-def test_edge_sizes(orc):
+@pytest.mark.parametrize("small", [512, 0])
+def test_edge_sizes(orc, small):
+    """Tiny D and N, on the small-population kernels and on the batched ones."""
     torch = _torch()
     for D in (2, 3, 11):
         cu = gu.ensure(D, 70)
+        cu.curob_set_small_batch(small)
         fids = [f for f in ALL if D >= 10 or not (23 <= f <= 28 or f >= 35)]
-        for fid in fids:
-            for N in (1, 33, 70):
-                x = inputs.uniform(N, D, N + fid)
-                ref = orc.evaluate(fid, D, 0, x)
-                got = gu.gpu_eval(fid, x, torch.float64)
-                assert np.all(gu.rel_err(got, ref) <= 1e-12), (D, fid, N)
+        try:
+            for fid in fids:
+                for N in (1, 33, 70):
+                    x = inputs.uniform(N, D, N + fid)
+                    ref = orc.evaluate(fid, D, 0, x)
+                    got = gu.gpu_eval(fid, x, torch.float64)
+                    assert np.all(gu.rel_err(got, ref) <= 1e-12), (D, fid, N)
+        finally:
+            cu.curob_set_small_batch(512)
 
 
 def test_errors_and_empty():
@@ -293,12 +299,14 @@ def test_composition_far_outside_the_box(orc):
             cu.curob_set_component(30, k, c.o, c.S, c.R)
         x = np.array([[2000.0, 0, 0, 0], [-5000.0, 100, 0, 7], [0, 0, 0, 3000.0]])
         ref = orc.evaluate_given(30, D, comps, x)
-        got = gu.gpu_eval(30, x, torch.float64)
-        assert np.all(np.isfinite(got))
-        assert np.all(gu.rel_err(got, ref) <= 1e-12), (got, ref)
         x32 = x.astype(np.float32)
-        got32 = gu.gpu_eval(30, x32, torch.float32)
         ref32 = orc.evaluate_given(30, D, comps, x32.astype(np.float64))
-        assert np.all(gu.rel_err(got32, ref32) <= 1e-5), (got32, ref32)
+        for small in (512, 0):  # the small-population kernels, then the batched ones
+            cu.curob_set_small_batch(small)
+            got = gu.gpu_eval(30, x, torch.float64)
+            assert np.all(np.isfinite(got))
+            assert np.all(gu.rel_err(got, ref) <= 1e-12), (small, got, ref)
+            got32 = gu.gpu_eval(30, x32, torch.float32)
+            assert np.all(gu.rel_err(got32, ref32) <= 1e-5), (small, got32, ref32)
     finally:
         gu.invalidate()
