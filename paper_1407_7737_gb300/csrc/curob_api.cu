@@ -11,6 +11,7 @@
 #include "curob_instance.hpp"
 #include "curob_internal.hpp"
 #include "curob_mma.hpp"
+#include "curob_small.cuh"
 
 namespace curob {
 namespace {
@@ -32,6 +33,7 @@ struct State {
   void* d_hout = nullptr; // (max_conc doubles)
   cudaStream_t hstream = nullptr;         // host wrappers: chunk 0's stream
   cudaStream_t hside[3] = {};             // and the other chunks' streams
+  SmallArgs small[kNumFunctions];         // launch arguments of the small kernels
 };
 
 // Host wrappers cut a call into up to kHostChunks chunks of whole 128-row
@@ -114,6 +116,16 @@ int resolve_precision(const Function& F) {
   if (mode == CUROB_PRECISION_AUTO)
     mode = mma_ok ? mma_auto_mode(g.inst.mma, F) : CUROB_PRECISION_SIMT;
   return mode;
+}
+
+// The small kernels' by-value copy of a function's segments and components.
+void make_small_args(SmallArgs& a, const Function& F) {
+  memset(&a, 0, sizeof(a));
+  a.tb = g.inst.tables();
+  a.F = F;
+  a.seg_base = g.inst.comps[F.comp0].seg0;
+  for (int i = 0; i < F.nseg && i < kSmallMaxWarps; ++i) a.seg[i] = g.inst.segs[a.seg_base + i];
+  for (int c = 0; c < F.ncomp; ++c) a.comp[c] = g.inst.comps[F.comp0 + c];
 }
 
 // A call of N candidates takes the small-population kernels (FP64, and the
@@ -201,6 +213,8 @@ curob_status curob_initialize(int D, int max_concurrency, uint64_t seed) {
   }
   g.precision = CUROB_PRECISION_AUTO;
   g.small_batch = kSmallBatchDefault;
+  for (int fid = 0; fid < kNumFunctions; ++fid)
+    if (g.inst.func_ok[fid]) make_small_args(g.small[fid], g.inst.func[fid]);
   g.init = true;
   return CUROB_OK;
 }
@@ -220,7 +234,7 @@ curob_status curob_evaluate(int fid, const double* x, int N, double* out, curob_
   if (!device_accessible(x) || !device_accessible(out)) return CUROB_ERR_INVALID_ARGUMENT;
   const Function& F = g.inst.func[fid];
   cudaError_t e = use_small(F, N)
-                      ? launch_small_f64(tables(), F, x, N, out, (cudaStream_t)stream)
+                      ? launch_small_f64(g.small[fid], x, N, out, (cudaStream_t)stream)
                       : launch_simt_f64(tables(), F, x, N, out, (cudaStream_t)stream);
   return e == cudaSuccess ? CUROB_OK : CUROB_ERR_CUDA;
 }
@@ -235,7 +249,7 @@ curob_status curob_evaluatef(int fid, const float* x, int N, float* out, curob_s
   if (mode < 0) return CUROB_ERR_UNSUPPORTED;
   cudaError_t e;
   if (g.precision == CUROB_PRECISION_AUTO && use_small(F, N))
-    e = launch_small_f32(tables(), F, x, N, out, (cudaStream_t)stream);
+    e = launch_small_f32(g.small[fid], x, N, out, (cudaStream_t)stream);
   else if (mode == CUROB_PRECISION_SIMT)
     e = launch_simt_f32(tables(), F, x, N, out, (cudaStream_t)stream);
   else if (mode == CUROB_PRECISION_MIXED)
@@ -254,7 +268,7 @@ curob_status curob_h_evaluate(int fid, const double* x, int N, double* out) {
   const Function& F = g.inst.func[fid];
   return host_pipeline<double>(x, N, out, [&](const double* dx, int n, double* dout,
                                               cudaStream_t st) {
-    const cudaError_t e = use_small(F, n) ? launch_small_f64(tables(), F, dx, n, dout, st)
+    const cudaError_t e = use_small(F, n) ? launch_small_f64(g.small[fid], dx, n, dout, st)
                                           : launch_simt_f64(tables(), F, dx, n, dout, st);
     return e == cudaSuccess ? CUROB_OK : CUROB_ERR_CUDA;
   });

@@ -80,6 +80,9 @@ struct Tables {
   const double* R;      // FP64 rotation blocks
   const float* R32;     // FP32 rounding of the rotation blocks (hi word)
   const float* R32lo;   // R - R32 rounded to FP32 (lo word)
+  const double* Rt;     // the same three, each block column-major (small-population
+  const float* R32t;    // kernels: lane i reads entry (i, j) at step j)
+  const float* R32lot;
   const double* aux;    // per-variable tables (FP64)
   const float* aux32;   // per-variable tables (FP32)
   const float* img;     // tensor-core operand images
@@ -529,6 +532,34 @@ __device__ inline double compose(const Component* comps, int nc, const double* G
   double Z = 0.0;
   for (int c = 0; c < nc; ++c) Z += exp(lw[c] - mx);
   for (int c = 0; c < nc; ++c) F += (exp(lw[c] - mx) / Z) * (comps[c].lambda * G[c] + comps[c].bias);
+  return F;
+}
+
+// compose() by one warp: lane c < nc forms member c's weight (FP64 costs the
+// same per warp instruction whatever the number of active lanes, so nc
+// weights take the time of one); lane 0 adds them and the members' values in
+// member order, as compose() does, so the value is the same.  Every lane of
+// the warp calls it; the result is lane 0's.
+__device__ inline double compose_warp(const Component* comps, int nc, const double* G,
+                                      const double* d2, int D) {
+  const int lane = threadIdx.x & 31;
+  int hit = -1;
+  for (int c = 0; c < nc; ++c)
+    if (d2[c] == 0.0 && hit < 0) hit = c;
+  if (hit >= 0) return comps[hit].lambda * G[hit] + comps[hit].bias;
+  double w = 0.0;
+  if (lane < nc) {
+    const double s = comps[lane].sigma;
+    w = (1.0 / sqrt(d2[lane])) * exp(-d2[lane] / (2.0 * (double)D * s * s));
+  }
+  double wc[kMaxComponents];
+#pragma unroll
+  for (int c = 0; c < kMaxComponents; ++c) wc[c] = __shfl_sync(0xffffffffu, w, c);
+  double W = 0.0;
+  for (int c = 0; c < nc; ++c) W += wc[c];
+  if (!(W > 0.0)) return compose(comps, nc, G, d2, D);  // log-domain branch (far outside)
+  double F = 0.0;
+  for (int c = 0; c < nc; ++c) F += (wc[c] / W) * (comps[c].lambda * G[c] + comps[c].bias);
   return F;
 }
 

@@ -292,6 +292,9 @@ curob_status Instance::generate_all() {
     fail(launch_gauss_gs(d_gj, (int)gj.size(), max_n, seed, d_R, d_status, 0));
   if (rc == CUROB_OK) fail(launch_aux(d_aj, (int)aj.size(), d_aux, d_aux32, 0));
   if (rc == CUROB_OK) fail(launch_split_f32(d_R, d_R32, d_R32lo, r_total, 0));
+  for (size_t i = 0; i < gj.size() && rc == CUROB_OK; ++i)
+    fail(launch_transpose_block(gj[i].r_off, gj[i].n, d_R, d_R32, d_R32lo, d_Rt, d_R32t,
+                                d_R32lot, 0));
   if (rc == CUROB_OK) fail(cudaDeviceSynchronize());
   cudaFree(d_pj); cudaFree(d_gj); cudaFree(d_aj); cudaFree(d_words); cudaFree(d_mark);
   if (rc == CUROB_OK) {
@@ -313,6 +316,9 @@ Tables Instance::tables() const {
   t.R = d_R;
   t.R32 = d_R32;
   t.R32lo = d_R32lo;
+  t.Rt = d_Rt;
+  t.R32t = d_R32t;
+  t.R32lot = d_R32lot;
   t.aux = d_aux;
   t.aux32 = d_aux32;
   t.img = mma.img;
@@ -324,6 +330,8 @@ Tables Instance::tables() const {
 void Instance::release() {
   cudaFree(d_seg); cudaFree(d_comp); cudaFree(d_o); cudaFree(d_operm);
   cudaFree(d_R); cudaFree(d_aux); cudaFree(d_S); cudaFree(d_R32); cudaFree(d_R32lo);
+  cudaFree(d_Rt); cudaFree(d_R32t); cudaFree(d_R32lot);
+  d_Rt = nullptr; d_R32t = d_R32lot = nullptr;
   cudaFree(d_aux32); cudaFree(d_status);
   mma_release(mma);
   d_seg = nullptr; d_comp = nullptr; d_o = d_operm = d_R = d_aux = nullptr;
@@ -349,6 +357,9 @@ curob_status Instance::create(int D_, uint64_t seed_) {
             alloc((void**)&d_R, sizeof(double) * (size_t)r_total) &&
             alloc((void**)&d_R32, sizeof(float) * (size_t)r_total) &&
             alloc((void**)&d_R32lo, sizeof(float) * (size_t)r_total) &&
+            alloc((void**)&d_Rt, sizeof(double) * (size_t)r_total) &&
+            alloc((void**)&d_R32t, sizeof(float) * (size_t)r_total) &&
+            alloc((void**)&d_R32lot, sizeof(float) * (size_t)r_total) &&
             alloc((void**)&d_aux, sizeof(double) * (size_t)aux_total) &&
             alloc((void**)&d_aux32, sizeof(float) * (size_t)aux_total) &&
             alloc((void**)&d_status, sizeof(int));
@@ -429,6 +440,7 @@ curob_status Instance::set_component(int fid, int comp, const double* o, const i
       const size_t nn = (size_t)s.n * s.n;
       CU_(cudaMemcpy(d_R + s.r_off, R + off, sizeof(double) * nn, cudaMemcpyHostToDevice));
       CU_(launch_split_f32(d_R + s.r_off, d_R32 + s.r_off, d_R32lo + s.r_off, (long long)nn, 0));
+      CU_(launch_transpose_block(s.r_off, s.n, d_R, d_R32, d_R32lo, d_Rt, d_R32t, d_R32lot, 0));
       off += (long long)nn;
     }
   }

@@ -34,6 +34,8 @@ class Instance {
   double *d_o = nullptr, *d_operm = nullptr, *d_R = nullptr, *d_aux = nullptr;
   int* d_S = nullptr;
   float *d_R32 = nullptr, *d_R32lo = nullptr, *d_aux32 = nullptr;
+  double* d_Rt = nullptr;  // column-major copies of the blocks
+  float *d_R32t = nullptr, *d_R32lot = nullptr;
   int* d_status = nullptr;
   long long r_total = 0, aux_total = 0;
   MmaPlan mma;  // tensor-core operand images

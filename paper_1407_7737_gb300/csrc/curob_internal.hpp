@@ -43,6 +43,9 @@ cudaError_t launch_aux(const AuxJob* d_jobs, int njobs, double* aux, float* aux3
                        cudaStream_t st);
 cudaError_t launch_split_f32(const double* src, float* hi, float* lo, long long n,
                              cudaStream_t st);
+cudaError_t launch_transpose_block(long long r_off, int n, const double* R, const float* Rh,
+                                   const float* Rl, double* Rt, float* Rht, float* Rlt,
+                                   cudaStream_t st);
 cudaError_t launch_operm(const PermJob* d_jobs, int njobs, int D, const double* o, const int* S,
                          double* operm, cudaStream_t st);
 
@@ -55,10 +58,11 @@ cudaError_t launch_simt_f32(const Tables& tb, const Function& F, const float* x,
 // curob_small64.cu / curob_small32.cu: one CTA per candidate and one warp
 // per block, for small populations; blocks up to 128 wide, at most 16 blocks
 // per function, the CTA's tables within 160 KB of shared memory.
+struct SmallArgs;  // curob_small.cuh
 bool small_supports(const Function& F, int D);
-cudaError_t launch_small_f64(const Tables& tb, const Function& F, const double* x, int N,
-                             double* out, cudaStream_t st);
-cudaError_t launch_small_f32(const Tables& tb, const Function& F, const float* x, int N,
-                             float* out, cudaStream_t st);
+cudaError_t launch_small_f64(const SmallArgs& a, const double* x, int N, double* out,
+                             cudaStream_t st);
+cudaError_t launch_small_f32(const SmallArgs& a, const float* x, int N, float* out,
+                             cudaStream_t st);
 
 }  // namespace curob

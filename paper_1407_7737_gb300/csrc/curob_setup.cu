@@ -3,6 +3,8 @@
 // Gaussian blocks orthonormalised by Gram-Schmidt, per-variable tables.
 // Not timed: runs once per curob_initialize.  Compiled with -fmad=false so
 // that the shift 140 u - 70 rounds exactly like its two-operation statement.
+#include <algorithm>
+
 #include "curob_internal.hpp"
 
 namespace curob {
@@ -152,7 +154,32 @@ __global__ void split_f32_kernel(const double* src, float* hi, float* lo, long l
   }
 }
 
+// Column-major copies of one rotation block (FP64 and the FP32 hi/lo words)
+// for the small-population kernels, whose lane i walks row i of the block:
+// in the copy, the lanes of one step read consecutive addresses.
+__global__ void transpose_block_kernel(long long r_off, int n, const double* R, const float* Rh,
+                                       const float* Rl, double* Rt, float* Rht, float* Rlt) {
+  const long long nn = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / n, j = e - i * n;
+    Rt[r_off + j * n + i] = R[r_off + e];
+    Rht[r_off + j * n + i] = Rh[r_off + e];
+    Rlt[r_off + j * n + i] = Rl[r_off + e];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_transpose_block(long long r_off, int n, const double* R, const float* Rh,
+                                   const float* Rl, double* Rt, float* Rht, float* Rlt,
+                                   cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const long long nn = (long long)n * n;
+  const int blocks = (int)std::min<long long>((nn + 255) / 256, 1024);
+  transpose_block_kernel<<<blocks, 256, 0, st>>>(r_off, n, R, Rh, Rl, Rt, Rht, Rlt);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_shift_perm(const PermJob* d_jobs, int njobs, int D, uint64_t seed, double* o,
                               int* S, double* operm, uint64_t* tmp_words, int* tmp_mark,

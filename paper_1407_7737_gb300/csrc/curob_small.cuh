@@ -57,7 +57,18 @@ struct SmallAccum {
 
 // Shared-memory layout of one CTA (offsets in bytes, all 8-byte aligned).
 struct SmallSmem {
-  size_t z, t, y, yl, p, d2, w, total;
+  size_t x, z, t, y, yl, p, d2, w, total;
+};
+
+// What a small-population launch reads of the instance, passed by value: the
+// function's segments and components sit in the kernel's parameter space,
+// so no warp waits on global memory for its block's descriptor.
+struct SmallArgs {
+  Tables tb;
+  Function F;
+  int seg_base;                     // the function's first segment in the table
+  Segment seg[kSmallMaxWarps];      // its segments, in table order
+  Component comp[kMaxComponents];   // its components
 };
 
 // T: element type of x; D the dimension.  FP64: z, y (ncomp x D doubles),
@@ -74,6 +85,7 @@ __host__ __device__ inline SmallSmem small_smem_layout(const Function& F, int D)
     off += (bytes + 15) / 16 * 16;
     return o;
   };
+  L.x = take(sizeof(T) * D);
   L.z = take(sizeof(T) * zd);
   L.y = take(sizeof(T) * zd);
   L.yl = take(sizeof(T) == 4 ? sizeof(float) * zd : 0);
@@ -88,8 +100,8 @@ __host__ __device__ inline SmallSmem small_smem_layout(const Function& F, int D)
 #ifdef CUROB_SMALL_F64
 // Steps 1-3 of one block in FP64 (warp-wide).
 __device__ inline void small_block_f64(const Tables& tb, const Segment& sg, const Component& C,
-                                       const double* __restrict__ xr, double* Zc, double* Yc,
-                                       double* Tc, double* W, double* d2p_out) {
+                                       const double* xs, double* Zc, double* Yc, double* Tc,
+                                       double* W, double* d2p_out) {
   const int lane = threadIdx.x & 31;
   const int D = tb.D;
   const int n = sg.n;
@@ -99,7 +111,7 @@ __device__ inline void small_block_f64(const Tables& tb, const Segment& sg, cons
   double d2p = 0.0;
   for (int j = lane; j < n; j += 32) {
     const double ov = op[sg.zoff + j];
-    const double d = xr[S[sg.zoff + j]] - ov;
+    const double d = xs[S[sg.zoff + j]] - ov;
     Yc[sg.zoff + j] = sg.scale * d;
     d2p += d * d;
   }
@@ -110,12 +122,12 @@ __device__ inline void small_block_f64(const Tables& tb, const Segment& sg, cons
   if (sg.identity) {
     for (int i = lane; i < n; i += 32) Zc[sg.zoff + i] = Yc[sg.zoff + i] + sg.offset;
   } else {
-    const double* __restrict__ Rb = tb.R + sg.r_off;
+    const double* __restrict__ Rt = tb.Rt + sg.r_off;  // column-major: (i, j) at j n + i
     const double* Yb = Yc + sg.zoff;
     for (int i = lane; i < n; i += 32) {
-      const double* Ri = Rb + (long long)i * n;
       double acc = 0.0;
-      for (int j = 0; j < n; ++j) acc = fma(Ri[j], Yb[j], acc);
+#pragma unroll 8
+      for (int j = 0; j < n; ++j) acc = fma(Rt[(long long)j * n + i], Yb[j], acc);
       Zc[sg.zoff + i] = acc + sg.offset;
     }
   }
@@ -161,14 +173,15 @@ __device__ inline void small_block_f64(const Tables& tb, const Segment& sg, cons
 
 // The component's sums in index order over its blocks (one thread), as the
 // batched FP64 kernel: returns G_c; *d2 = ||x - o_c||^2 block after block.
-__device__ inline double small_close_f64(const Tables& tb, const Component& C, int seg_base,
+__device__ inline double small_close_f64(const SmallArgs& a, const Component& C,
                                          const double* Zc, const double* Tc, const double* d2s,
                                          double* d2) {
-  const int D = tb.D;
+  const int D = a.tb.D;
+  const int seg_base = a.seg_base;
   SmallAccum st;
   double dd = 0.0;
   for (int si = 0; si < C.nseg; ++si) {
-    const Segment sg = tb.seg[C.seg0 + si];
+    const Segment& sg = a.seg[C.seg0 - seg_base + si];
     dd += d2s[C.seg0 - seg_base + si];
     const int n = sg.n, kind = sg.kind;
     const bool pairs = kind_has_pairs(kind);
@@ -215,8 +228,8 @@ __device__ inline double small_close_f64(const Tables& tb, const Component& C, i
 // Steps 1-3 of one block on the FP32 path (warp-wide); the block's four FP64
 // partial sums go to P[0..3].
 __device__ inline void small_block_f32(const Tables& tb, const Segment& sg, const Component& C,
-                                       const float* __restrict__ xr, float* Uc, float* Yh,
-                                       float* Yl, double* P, double* d2p_out) {
+                                       const float* xs, float* Uc, float* Yh, float* Yl,
+                                       double* P, double* d2p_out) {
   const int lane = threadIdx.x & 31;
   const int n = sg.n;
   const int* __restrict__ S = tb.S + C.base;
@@ -225,7 +238,7 @@ __device__ inline void small_block_f32(const Tables& tb, const Segment& sg, cons
   double d2p = 0.0;
   for (int j = lane; j < n; j += 32) {
     const double ov = op[sg.zoff + j];
-    const double d = (double)xr[S[sg.zoff + j]] - ov;
+    const double d = (double)xs[S[sg.zoff + j]] - ov;
     const double y = sg.scale * d;
     const float yh = (float)y;
     Yh[sg.zoff + j] = yh;
@@ -242,21 +255,20 @@ __device__ inline void small_block_f32(const Tables& tb, const Segment& sg, cons
   if (sg.identity) {
     for (int i = lane; i < n; i += 32) Ub[i] = yh[i] + yl[i];
   } else {
-    const float* __restrict__ Rh = tb.R32 + sg.r_off;
-    const float* __restrict__ Rl = tb.R32lo + sg.r_off;
+    const float* __restrict__ Rh = tb.R32t + sg.r_off;   // column-major: (i, j) at j n + i
+    const float* __restrict__ Rl = tb.R32lot + sg.r_off;
     for (int i = lane; i < n; i += 32) {
-      const float* rh = Rh + (long long)i * n;
-      const float* rl = Rl + (long long)i * n;
       float s = 0.f, c = 0.f;
+#pragma unroll 8
       for (int j = 0; j < n; ++j) {
-        const float a = rh[j], b = yh[j];
+        const float a = Rh[(long long)j * n + i], b = yh[j];
         const float p = a * b;
         const float e = fmaf(a, b, -p);                // a*b = p + e exactly
         const float t = s + p;
         const float bb = t - s;
         const float err = (s - (t - bb)) + (p - bb);   // s + p = t + err exactly
         s = t;
-        c += err + e + fmaf(a, yl[j], rl[j] * b);
+        c += err + e + fmaf(a, yl[j], Rl[(long long)j * n + i] * b);
       }
       Ub[i] = s + c;
     }
@@ -274,8 +286,12 @@ __device__ inline void small_block_f32(const Tables& tb, const Segment& sg, cons
     elem_term_f32(kind, zi, ui, sg.gpos + i, gnT, has_aux ? aux[i] : 0.f, sg.kat_e, a);
     if (pairs && i + 1 < n) a.a0 += pair_term<float>(kind, zi, Ub[i + 1] + off);
   }
-  const double r0 = small_warp_sum((double)a.a0), r1 = small_warp_sum((double)a.a1);
-  const double r2 = small_warp_sum((double)a.a2), rp = small_warp_prod((double)a.p);
+  // FP64 across the lanes only for the sums the kind uses (each FP64 warp
+  // instruction costs the same as 32 lanes' worth)
+  const double r0 = small_warp_sum((double)a.a0);
+  const double r1 = kind_uses_a1(kind) ? small_warp_sum((double)a.a1) : 0.0;
+  const double r2 = kind_uses_a2(kind) ? small_warp_sum((double)a.a2) : 0.0;
+  const double rp = kind_uses_p(kind) ? small_warp_prod((double)a.p) : 1.0;
   if (lane == 0) {
     P[0] = r0;
     P[1] = r1;
@@ -286,13 +302,14 @@ __device__ inline void small_block_f32(const Tables& tb, const Segment& sg, cons
 
 // The component's blocks in order (one thread), as the batched CUDA-core
 // FP32 kernel: returns G_c; *d2 = ||x - o_c||^2 block after block.
-__device__ inline double small_close_f32(const Tables& tb, const Component& C, int seg_base,
+__device__ inline double small_close_f32(const SmallArgs& a, const Component& C,
                                          const float* Uc, const double* P, const double* d2s,
                                          double* d2) {
+  const int seg_base = a.seg_base;
   SmallAccum st;
   double dd = 0.0;
   for (int si = 0; si < C.nseg; ++si) {
-    const Segment sg = tb.seg[C.seg0 + si];
+    const Segment& sg = a.seg[C.seg0 - seg_base + si];
     const int g = C.seg0 - seg_base + si;
     dd += d2s[g];
     const int kind = sg.kind;
