@@ -156,14 +156,17 @@ curob_status curob_query_small(int fid, int N, int* small);
 curob_status curob_query_precision(int fid, int* mode);
 
 /* Number of kernel launches curob_evaluatef(fid, ., N, ., .) makes under the
- * current precision: 1 for a function whose blocks are all evaluated in the
- * tensor-core epilogue; one per precision group plus a finish kernel when a
- * block has a heavy kind (Powers, Weierstrass, Griewank, Schaffer F7,
- * expanded Griewank-Rosenbrock, Modified Schwefel, Katsuura, expanded
- * Schaffer F6: their terms run in a separate kernel over z) or the function
- * is a MIXED composition; times the number of candidate slices (scratch is
- * bounded to 256 MB per slice).  Errors: as curob_query_precision, and
- * INVALID_ARGUMENT for N < 0. */
+ * current precision.  On the tensor cores, per slice of candidates (the
+ * heavy-kind scratch is bounded to 256 MB per slice): one that transposes
+ * the slice of x (the tensor-core kernels fetch each stage's variables as
+ * rows of x^T), one per precision group, and a finish kernel when a block
+ * has a heavy kind (Powers, Weierstrass, Griewank, Schaffer F7, expanded
+ * Griewank-Rosenbrock, Modified Schwefel, Katsuura, expanded Schaffer F6:
+ * their terms run in a separate kernel over z) or the function is a MIXED
+ * composition.  1 on the CUDA-core and small-population kernels.  (If the
+ * stream-ordered scratch cannot be had, a call makes fewer: no transpose, or
+ * one fused launch.)  Errors: as curob_query_precision, and INVALID_ARGUMENT
+ * for N < 0. */
 curob_status curob_query_launches(int fid, int N, int* launches);
 
 /* The precision component `comp` of fid runs at (the same as

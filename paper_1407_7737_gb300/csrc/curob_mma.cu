@@ -61,6 +61,7 @@
 
 #include "curob_mma.hpp"
 #include "curob_tc.cuh"
+#include "curob_tmap.hpp"
 
 namespace curob {
 namespace {
@@ -73,10 +74,12 @@ constexpr int kTileM = 128;
 constexpr size_t kScratchCap = size_t(256) << 20;
 
 constexpr int kThreads = 448;  // 8 producer, 4 epilogue, MMA and loader warps
-constexpr int kMmaWarp = 12, kLoaderWarp = 13;
+constexpr int kThreadsXT = 480;  // the same and the raw-gather warp (x^T launches)
+constexpr int kMmaWarp = 12, kLoaderWarp = 13, kRawWarp = 14;
 constexpr int kMaxNpad = 512;                    // TMEM columns
 constexpr int kExactMaxNC = 192;                 // EXACT: widest N chunk
 constexpr int kMaxStages = 6;                    // K stages in flight
+constexpr int kMaxARing = 8;                     // A slots of the transposed-input rings
 constexpr int kCtrlHeader = 512;                 // barrier header of the control block
 constexpr size_t kSmemCap = 227 * 1024 - 1024;   // dynamic shared memory, less alignment slack
 constexpr int kExactAcc1 = 256;                  // EXACT: TMEM column of accumulator 1
@@ -141,6 +144,13 @@ struct MmaArgs {
   const float* onat;     // EXACT: o per component in natural order, FP32
   int nstage;
   int stage_bytes;
+  // Operand rings.  Batched launches read x with gathers into the A area of
+  // each stage (A and B of a stage side by side: nA = nB = nstage).  Launches
+  // on the transposed copy of x (xt = 1) keep separate rings: nA A slots of
+  // a_bytes (the raw gather lands in the slot it is converted in) and nB B
+  // slots of b_bytes.
+  int xt;
+  int nA, a_bytes, nB, b_bytes;
   int nlist;                   // components evaluated, in order (all of F's, or a subset)
   int list[kMaxComponents];
   double* gout;                // split launches: G_c and ||x - o_c||^2 per component and row
@@ -327,6 +337,9 @@ __device__ __forceinline__ void epi_chunk(int kind, const float* v, int c, int c
 // persistent kernels).
 struct Smem {
   uint8_t* stages;
+  uint8_t *a_base, *b_base;  // A slot s at a_base + s a_stride, B slot at b_base + s b_stride
+  int a_stride, b_stride, nA, nB;
+  uint64_t *fullB, *emptyB, *rawfull;  // B ring (aliases full/empty unless xt), raw gathers
   uint64_t *full, *empty, *tmem_full, *tmem_empty, *sig_full, *prod_bar, *gbar;
   uint32_t* tmem_slot;
   volatile int* abort_flag;
@@ -338,19 +351,52 @@ struct Smem {
   int* item;  // persistent kernel: the work item of the CTA
 };
 
-__device__ inline Smem smem_map(uint8_t* smem_raw, int nstage, int stage_bytes) {
+// Ring geometry of a launch: xt = 0 (nstage stages of stage_bytes, A of
+// a_bytes first in each) or xt = 1 (separate A and B rings).
+struct RingGeom {
+  int xt, nstage, stage_bytes, nA, a_bytes, nB, b_bytes;
+};
+
+__device__ inline Smem smem_map(uint8_t* smem_raw, const RingGeom& g) {
   Smem m;
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   m.stages = smem;
-  uint8_t* ctrl = smem + (size_t)nstage * stage_bytes;
+  uint8_t* ctrl;
+  if (g.xt) {
+    m.nA = g.nA;
+    m.nB = g.nB;
+    m.a_base = smem;
+    m.a_stride = g.a_bytes;
+    m.b_base = smem + (size_t)g.nA * g.a_bytes;
+    m.b_stride = g.b_bytes;
+    ctrl = m.b_base + (size_t)g.nB * g.b_bytes;
+  } else {
+    m.nA = m.nB = g.nstage;
+    m.a_base = smem;
+    m.b_base = smem + g.a_bytes;
+    m.a_stride = m.b_stride = g.stage_bytes;
+    ctrl = smem + (size_t)g.nstage * g.stage_bytes;
+  }
+  const int nA = m.nA, nB = m.nB;
   m.full = reinterpret_cast<uint64_t*>(ctrl);
-  m.empty = m.full + nstage;
-  m.tmem_full = m.empty + nstage;
+  m.empty = m.full + nA;
+  m.tmem_full = m.empty + nA;
   m.tmem_empty = m.tmem_full + 1;
   m.sig_full = m.tmem_empty + 1;  // [kSigRing]
   m.prod_bar = m.sig_full + kSigRing;
-  m.gbar = m.prod_bar + 1;        // [nstage]
-  m.tmem_slot = reinterpret_cast<uint32_t*>(m.gbar + nstage);
+  m.gbar = m.prod_bar + 1;        // [nA]
+  uint64_t* next = m.gbar + nA;
+  if (g.xt) {
+    m.fullB = next;               // [nB]
+    m.emptyB = m.fullB + nB;      // [nB]
+    m.rawfull = m.emptyB + nB;    // [nA]
+    next = m.rawfull + nA;
+  } else {
+    m.fullB = m.full;
+    m.emptyB = m.empty;
+    m.rawfull = nullptr;
+  }
+  m.tmem_slot = reinterpret_cast<uint32_t*>(next);
   m.abort_flag = reinterpret_cast<volatile int*>(m.tmem_slot + 1);
   m.item = const_cast<int*>(reinterpret_cast<volatile int*>(m.abort_flag) + 1);
   m.rowG = reinterpret_cast<double*>(ctrl + kCtrlHeader);         // [kMaxComponents][128]
@@ -370,16 +416,23 @@ struct RoleState {
   uint32_t pphase = 0;    // producer group barrier uses
   uint32_t comp_it = 0;   // components (row-scale ring)
   uint32_t b_par = 0;     // B loads: bit s = parity of stage s's last load, bit 8 + s = used
+  uint32_t r_par = 0;     // raw gathers (xt), the same bookkeeping per A slot
 };
 
-__device__ inline void cta_setup(const Smem& m, int nstage) {
+__device__ inline void cta_setup(const Smem& m, int xt) {
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < nstage; ++s) {
-      mbar_init(&m.full[s], 9);   // 8 producer warps + the B loader's expect_tx
-      mbar_init(&m.empty[s], 1);  // one tcgen05.commit
-      mbar_init(&m.gbar[s], 256); // producer threads' cp.async
+    for (int s = 0; s < m.nA; ++s) {
+      mbar_init(&m.full[s], xt ? 8 : 9);  // 8 producer warps (+ the B loader's expect_tx)
+      mbar_init(&m.empty[s], 1);          // one tcgen05.commit
+      mbar_init(&m.gbar[s], 256);         // producer threads' cp.async
+      if (xt) mbar_init(&m.rawfull[s], 1);  // the raw gathers' expect_tx
     }
+    if (xt)
+      for (int s = 0; s < m.nB; ++s) {
+        mbar_init(&m.fullB[s], 1);   // the B loader's expect_tx
+        mbar_init(&m.emptyB[s], 1);  // one tcgen05.commit
+      }
     mbar_init(m.tmem_full, 1);
     mbar_init(m.tmem_empty, 4);   // the 4 epilogue warps
     for (int s = 0; s < kSigRing; ++s) mbar_init(&m.sig_full[s], 4);  // producer warps 0-3
@@ -465,8 +518,11 @@ __device__ inline void cta_teardown(const Smem& m) {
   (void)tabS; (void)tabH; (void)tabL; (void)tmem_base; (void)D; (void)stages; \
   (void)warp;
 
-template <int kMode>
-__device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, RoleState& rs) {
+// kXT: x comes from its transposed copy by TMA gathers (see MmaArgs::xt);
+// each producer warp then owns rows 16 w .. 16 w + 15, two lanes per row.
+template <int kMode, bool kXT>
+__device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, RoleState& rs,
+                              const CUtensorMap* xmap) {
   CUROB_ROLE_PROLOGUE
     // ------------------------------------------------------------ producers
     // Eight warps: warp w takes rows 32 (w % 4) .. + 31 (thread = candidate
@@ -477,6 +533,7 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
     // reads only its own raw values back, and no other thread touches them.
     const int h = warp >> 2;                 // half of the stage's columns
     const int r = (warp & 3) * 32 + lane;    // candidate row in the tile
+    (void)xmap;
     constexpr int kHalf = kKs / 2;           // columns per half
     constexpr int kCpp = kRow / 32;          // 16-byte chunks per part row per half
     const long long grow = row0 + r;
@@ -491,7 +548,7 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
     uint32_t& it = rs.it;
     uint32_t& pphase = rs.pphase;
     bool ok = true;
-    if (vrow && h == 0) {  // bring the row into L2 now: the gathers then wait on L2, not HBM
+    if (!kXT && vrow && h == 0) {  // bring the row into L2 now: the gathers then wait on L2
       const uintptr_t s0 = (reinterpret_cast<uintptr_t>(xrow) + 15) & ~uintptr_t(15);
       const uintptr_t s1 = reinterpret_cast<uintptr_t>(xrow + D) & ~uintptr_t(15);
       if (s1 > s0)
@@ -514,8 +571,9 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
         // rowMx and are read after the next producer barrier
         const float* on = a.onat + Cm.base;
         const bool vec = (D & 3) == 0 && (reinterpret_cast<uintptr_t>(a.x) & 15u) == 0;
+        const int hm = warp >> 2;
 #pragma unroll 2
-        for (int rr = 16 * h; rr < 16 * h + 16; ++rr) {
+        for (int rr = 16 * hm; rr < 16 * hm + 16; ++rr) {
           const int row = (warp & 3) * 32 + rr;
           const long long gr = row0 + row;
           float mv = 0.f;
@@ -568,6 +626,135 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
         const int nchunk = kMode == M_EXACT ? exact_nchunk(sg.npad) : 1;
         const int total = nslab * nchunk;  // stages of this block
         const uint32_t it0 = it;
+        if constexpr (kXT) {
+          const int nvalid = sg.n;
+          const int nA = m.nA;
+          constexpr int kRawBytes = kKs * kTileM * 4;
+          const uint32_t it0 = it;
+          // The raw x of a stage (its kKs variables x the tile's 128
+          // candidates, variable-major; gathered by the raw-gather warp) lies
+          // in the last bytes of the A slot it is converted in; the producers
+          // read it all, meet, and only then overwrite it with the operands.
+          auto raw_ptr = [&](uint32_t g) -> uint8_t* {
+            return m.a_base + (size_t)(g % nA) * m.a_stride + kParts * kPart - kRawBytes;
+          };
+          (void)it0;
+          for (int q = 0; q < total && ok; ++q, ++it) {
+            const int stage = it % nA;
+            uint8_t* A = m.a_base + (size_t)stage * m.a_stride;
+            const int t = q % nslab;
+            const bool good = mbar_wait(&m.rawfull[stage], (it / nA) & 1u, abort_flag, tb.status);
+            if (!__all_sync(0xffffffffu, good)) {
+              ok = false;
+              break;
+            }
+            // this thread's raw x: variables h kHalf + i of the stage at its row
+            float xv[kHalf];
+            {
+              const float* raw = reinterpret_cast<const float*>(raw_ptr(it));
+#pragma unroll
+              for (int i = 0; i < kHalf; ++i) {
+                const int v = h * kHalf + i;
+                const float val = raw[v * kTileM + r];
+                xv[i] = (t * kKs + v < nvalid) ? val : 0.f;  // a column past the block: x = 0
+              }
+            }
+            // all raw values are read before any producer overwrites them
+            if (!__all_sync(0xffffffffu, producers_sync(prod_bar, pphase, abort_flag, tb.status))) {
+              ok = false;
+              break;
+            }
+          constexpr int kPer = 16 / kEl;  // elements per 16-byte chunk
+          float d2p = 0.f;
+          // this half's kCpp chunks of 16 bytes per part row, each stored whole
+#pragma unroll
+          for (int cc = 0; cc < kCpp; ++cc) {
+            const int c = h * kCpp + cc;  // chunk of the row
+            float yh[kPer], yl[kPer], oh[kPer], ol[kPer];
+            const int jc = t * kKs + h * kHalf + cc * kPer;  // first column of the chunk
+#pragma unroll
+            for (int q4 = 0; q4 < kPer / 4; ++q4) {  // o words, 16 bytes at a time
+              const float4 a4 = *reinterpret_cast<const float4*>(tabH + jc + 4 * q4);
+              const float4 b4 = *reinterpret_cast<const float4*>(tabL + jc + 4 * q4);
+              oh[4 * q4] = a4.x; oh[4 * q4 + 1] = a4.y; oh[4 * q4 + 2] = a4.z; oh[4 * q4 + 3] = a4.w;
+              ol[4 * q4] = b4.x; ol[4 * q4 + 1] = b4.y; ol[4 * q4 + 2] = b4.z; ol[4 * q4 + 3] = b4.w;
+            }
+#pragma unroll
+            for (int e = 0; e < kPer; ++e) {
+              // branch-free, so that the chunk's elements interleave.  A
+              // column past the block has x = 0 (zero-filled copy) and o = 0
+              // (staged), so y = 0; a row past the batch is never written.
+              shift_ff(xv[cc * kPer + e], oh[e], ol[e], yh[e], yl[e]);
+              d2p = fmaf(yh[e], yh[e], d2p);
+            }
+            const uint32_t off = swz_m<kMode>((uint32_t)r, (uint32_t)(c * 16));
+            if constexpr (kMode == M_TF32) {
+              uint32_t hw[4], lw[4];
+#pragma unroll
+              for (int qq = 0; qq < 4; ++qq) {
+                const float a = yh[qq];
+                hw[qq] = to_tf32(a);
+                lw[qq] = to_tf32((a - __uint_as_float(hw[qq])) + yl[qq]);
+              }
+              *reinterpret_cast<uint4*>(A + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+              *reinterpret_cast<uint4*>(A + kPart + off) =
+                  make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            } else if constexpr (kMode == M_BF16) {
+              uint32_t hw[4], lw[4];
+#pragma unroll
+              for (int qq = 0; qq < 4; ++qq) {
+                const float a = yh[2 * qq], b = yh[2 * qq + 1];
+                hw[qq] = pack_bf16(a, b);
+                const float2 hf = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&hw[qq]));
+                lw[qq] = pack_bf16((a - hf.x) + yl[2 * qq], (b - hf.y) + yl[2 * qq + 1]);
+              }
+              *reinterpret_cast<uint4*>(A + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+              *reinterpret_cast<uint4*>(A + kPart + off) =
+                  make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            } else {
+              // four slices of v = 128 y / sigma (exact in BF16), already at
+              // their weight: s1 = rint(v), then the remainder r = v - s1
+              // (plus y's low word) rounded to multiples of 2^-8, 2^-16 and
+              // 2^-24 in turn.  Adding and subtracting 1.5 * 2^(23 - 8a)
+              // rounds to a multiple of 2^-8a, ties to even, exactly as rintf
+              // of the 2^8a-scaled value does (|v| < 128, |r| <= 2^-1, 2^-9,
+              // 2^-17), and every remainder is exact
+              const float s128 = isig * 128.f;
+              uint32_t w[4][4];
+#pragma unroll
+              for (int qq = 0; qq < 4; ++qq) {
+                float sl[2][4];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                  const int k = 2 * qq + e;
+                  const float v = yh[k] * s128;
+                  const float y1 = (v + 12582912.0f) - 12582912.0f;       // 1.5 * 2^23
+                  float rr = fmaf(yl[k], s128, v - y1);
+                  const float y2 = (rr + 49152.0f) - 49152.0f;            // 1.5 * 2^15
+                  rr = rr - y2;
+                  const float y3 = (rr + 192.0f) - 192.0f;                // 1.5 * 2^7
+                  rr = rr - y3;
+                  const float y4 = (rr + 0.75f) - 0.75f;                  // 1.5 * 2^-1
+                  sl[e][0] = y1;
+                  sl[e][1] = y2;
+                  sl[e][2] = y3;
+                  sl[e][3] = y4;
+                }
+#pragma unroll
+                for (int pp = 0; pp < 4; ++pp) w[pp][qq] = pack_bf16(sl[0][pp], sl[1][pp]);
+              }
+#pragma unroll
+              for (int pp = 0; pp < 4; ++pp)
+                *reinterpret_cast<uint4*>(A + pp * kPart + off) =
+                    make_uint4(w[pp][0], w[pp][1], w[pp][2], w[pp][3]);
+            }
+          }
+            if (q < nslab) d2 += (double)d2p;  // first chunk: ||x - o||^2 of the row
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full[stage]);
+          }
+        } else {
         // raw x of stage q: half h's column i goes to 16-byte chunk
         // (h kCpp + (i / 4) % kCpp) of part (i / 4) / kCpp of the row, in the
         // operand's swizzle.  Lanes walk rows' (sorted) columns, so one
@@ -736,6 +923,7 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
           if (lane == 0) mbar_arrive(&full[stage]);
           if (!early && q + P < total) ok = issue(q + P);
         }
+        }
       }
       rowD2[(h * kMaxComponents + ci) * kTileM + r] = d2;  // each half's share
     }
@@ -884,15 +1072,19 @@ __device__ void mma_tile(const MmaArgs& a, const Smem& m, long long row0, RoleSt
             tc_fence_after();
             const uint32_t ab = (chunk_it & 1u) ? (uint32_t)a.acc_hi : 0u;  // accumulator region
             for (int t = 0; t < nslab; ++t, ++it) {
-              const int stage = it % a.nstage;
-              const uint32_t ph = (it / a.nstage) & 1u;
-              if (!mbar_wait(&full[stage], ph, abort_flag, tb.status)) {
+              const int sA = it % m.nA, sB = it % m.nB;
+              if (!mbar_wait(&full[sA], (it / m.nA) & 1u, abort_flag, tb.status)) {
+                ok = false;
+                break;
+              }
+              if (m.fullB != m.full &&
+                  !mbar_wait(&m.fullB[sB], (it / m.nB) & 1u, abort_flag, tb.status)) {
                 ok = false;
                 break;
               }
               tc_fence_after();
-              const uint32_t sa = smem_u32(stages + (size_t)stage * a.stage_bytes);
-              const uint32_t sb = sa + kParts * kPart;
+              const uint32_t sa = smem_u32(m.a_base + (size_t)sA * m.a_stride);
+              const uint32_t sb = smem_u32(m.b_base + (size_t)sB * m.b_stride);
               const uint32_t bpart = (uint32_t)(nc * kRow);
 #pragma unroll
               for (int kk = 0; kk < kKsteps; ++kk) {
@@ -923,7 +1115,8 @@ __device__ void mma_tile(const MmaArgs& a, const Smem& m, long long row0, RoleSt
                   }
                 }
               }
-              tc_commit(&empty[stage]);  // frees the stage when these MMAs retire
+              tc_commit(&empty[sA]);  // frees the stage when these MMAs retire
+              if (m.emptyB != m.empty) tc_commit(&m.emptyB[sB]);
             }
             if (ok) tc_commit(tmem_full);  // this chunk's accumulators complete
           }
@@ -955,16 +1148,16 @@ __device__ void loader_tile(const MmaArgs& a, const Smem& m, long long row0, Rol
             const uint32_t bytes = (uint32_t)(kParts * nc * kRow);
             const uint8_t* src = base + (size_t)cc * nslab * kParts * nw * kRow;
             for (int t = 0; t < nslab; ++t, ++it) {
-              const int stage = it % a.nstage;
-              const uint32_t ph = (it / a.nstage) & 1u;
-              if (!mbar_wait(&empty[stage], ph ^ 1u, abort_flag, tb.status)) {
+              const int stage = it % m.nB;
+              const uint32_t ph = (it / m.nB) & 1u;
+              if (!mbar_wait(&m.emptyB[stage], ph ^ 1u, abort_flag, tb.status)) {
                 ok = false;
                 break;
               }
-              uint8_t* dst = stages + (size_t)stage * a.stage_bytes + kParts * kPart;
-              mbar_arrive_expect_tx(&full[stage], bytes);
+              uint8_t* dst = m.b_base + (size_t)stage * m.b_stride;
+              mbar_arrive_expect_tx(&m.fullB[stage], bytes);
               rs.b_par = (rs.b_par & ~(1u << stage)) | (ph << stage) | (1u << (stage + 8));
-              bulk_g2s(dst, src + (size_t)t * bytes, bytes, &full[stage]);
+              bulk_g2s(dst, src + (size_t)t * bytes, bytes, &m.fullB[stage]);
             }
           }
         }
@@ -973,19 +1166,76 @@ __device__ void loader_tile(const MmaArgs& a, const Smem& m, long long row0, Rol
     __syncwarp();
 }
 
-template <int kMode, bool kHeavy>
-__device__ inline void run_tile(const MmaArgs& a, const Smem& m, long long row0, RoleState& rs) {
+// x^T launches: lane 0 of the raw-gather warp walks the tile's K stages in
+// the producers' order and gathers each stage's variables (rows of x^T, the
+// tile's 128 candidates each, four rows per TMA gather) into the A slot the
+// stage will be converted in, as soon as the MMAs of that slot's previous
+// stage have retired.  The block's variable indices come straight from the
+// instance, so the warp runs ahead of the producers across block
+// boundaries.
+template <int kMode>
+__device__ void raw_loader_tile(const MmaArgs& a, const Smem& m, long long row0, RoleState& rs,
+                                const CUtensorMap* xmap) {
+  CUROB_ROLE_PROLOGUE
+  constexpr int kRawBytes = kKs * kTileM * 4;
+  constexpr int kGat = kKs / 4;
+  if (lane == 0) {
+    uint32_t& it = rs.it;
+    const int nA = m.nA;
+    bool ok = true;
+    for (int li = 0; li < a.nlist && ok && !*abort_flag; ++li) {
+      const Component Cm = tb.comp[F.comp0 + a.list[li]];
+      for (int si = 0; si < Cm.nseg && ok; ++si) {
+        const Segment sg = tb.seg[Cm.seg0 + si];
+        const int* S = tb.S + Cm.base + sg.zoff;
+        const int nslab = sg.npad / kKs;
+        const int nchunk = kMode == M_EXACT ? exact_nchunk(sg.npad) : 1;
+        const int total = nslab * nchunk;
+        for (int q = 0; q < total; ++q, ++it) {
+          const int t = q % nslab;
+          int rr[kKs];  // the stage's variables (loads in flight during the wait)
+#pragma unroll
+          for (int e = 0; e < kKs; ++e) {
+            const int j = t * kKs + e;
+            rr[e] = __ldg(S + (j < sg.n ? j : 0));
+          }
+          const int slot = it % nA;
+          if (!mbar_wait(&empty[slot], ((it / nA) & 1u) ^ 1u, abort_flag, tb.status)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&m.rawfull[slot], (uint32_t)kRawBytes);
+          rs.r_par = (rs.r_par & ~(1u << slot)) | (((it / nA) & 1u) << slot) | (1u << (slot + 8));
+          uint8_t* dst = m.a_base + (size_t)slot * m.a_stride + kParts * kPart - kRawBytes;
+#pragma unroll
+          for (int gg = 0; gg < kGat; ++gg)
+            tma_gather4(dst + gg * 4 * kTileM * 4, xmap, (int)row0, rr[4 * gg], rr[4 * gg + 1],
+                        rr[4 * gg + 2], rr[4 * gg + 3], &m.rawfull[slot]);
+        }
+      }
+    }
+  }
+  __syncwarp();
+}
+
+template <int kMode, bool kHeavy, bool kXT>
+__device__ inline void run_tile(const MmaArgs& a, const Smem& m, long long row0, RoleState& rs,
+                                const CUtensorMap* xmap) {
   const int warp = threadIdx.x >> 5;
-  if (warp < 8) producer_tile<kMode>(a, m, row0, rs);
+  if (warp < 8) producer_tile<kMode, kXT>(a, m, row0, rs, xmap);
   else if (warp < 12) epilogue_tile<kMode, kHeavy>(a, m, row0, rs);
   else if (warp == kMmaWarp) mma_tile<kMode>(a, m, row0, rs);
-  else loader_tile<kMode>(a, m, row0, rs);
+  else if (warp == kLoaderWarp) loader_tile<kMode>(a, m, row0, rs);
+  else if constexpr (kXT) raw_loader_tile<kMode>(a, m, row0, rs, xmap);
   if (*m.abort_flag) {  // no copy may still be landing when the CTA moves on or exits
     const unsigned long long deadline = globaltimer() + kTimeoutNs;
     if (warp < 8) asm volatile("cp.async.wait_all;" ::: "memory");
     if (warp == kLoaderWarp && (threadIdx.x & 31) == 0)
-      for (int s = 0; s < a.nstage; ++s)
-        if (rs.b_par >> (s + 8) & 1u) mbar_drain(&m.full[s], rs.b_par >> s & 1u, deadline);
+      for (int s = 0; s < m.nB; ++s)
+        if (rs.b_par >> (s + 8) & 1u) mbar_drain(&m.fullB[s], rs.b_par >> s & 1u, deadline);
+    if (kXT && warp == kRawWarp && (threadIdx.x & 31) == 0)  // the raw gathers' issuer
+      for (int s = 0; s < m.nA; ++s)
+        if (rs.r_par >> (s + 8) & 1u) mbar_drain(&m.rawfull[s], rs.r_par >> s & 1u, deadline);
   }
   // every issued MMA has been consumed by the epilogue (or the CTA aborted)
   tc_fence_before();
@@ -995,13 +1245,16 @@ __device__ inline void run_tile(const MmaArgs& a, const Smem& m, long long row0,
 }
 
 // One launch per function: CTA b evaluates candidates [128 b, 128 b + 128).
-template <int kMode, bool kHeavy>
-__global__ void __launch_bounds__(kThreads, 1) mma_eval_kernel(MmaArgs args) {
+template <int kMode, bool kHeavy, bool kXT>
+__global__ void __launch_bounds__(kXT ? kThreadsXT : kThreads, 1)
+mma_eval_kernel(MmaArgs args, const __grid_constant__ CUtensorMap xmap) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  const Smem m = smem_map(smem_raw, args.nstage, args.stage_bytes);
-  cta_setup(m, args.nstage);
+  const Smem m = smem_map(smem_raw, RingGeom{args.xt, args.nstage, args.stage_bytes, args.nA,
+                                             args.a_bytes, args.nB, args.b_bytes});
+  cta_setup(m, args.xt);
+  if (kXT && threadIdx.x == 0) tma_prefetch_desc(&xmap);
   RoleState rs;
-  run_tile<kMode, kHeavy>(args, m, (long long)blockIdx.x * kTileM, rs);
+  run_tile<kMode, kHeavy, kXT>(args, m, (long long)blockIdx.x * kTileM, rs, &xmap);
   cta_teardown(m);
 }
 
@@ -1014,8 +1267,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 mma_batch_kernel(const MmaArgs* __restrict__ insts, const int2* __restrict__ work, int nwork,
                  int* counter, int nstage, int stage_bytes) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  const Smem m = smem_map(smem_raw, nstage, stage_bytes);
-  cta_setup(m, nstage);
+  constexpr int kA = MC<kMode>::kParts * MC<kMode>::kPart;
+  const Smem m = smem_map(smem_raw, RingGeom{0, nstage, stage_bytes, nstage, kA, nstage,
+                                             stage_bytes - kA});
+  cta_setup(m, 0);
   RoleState rs;
   for (;;) {
     if (threadIdx.x == 0) *m.item = atomicAdd(counter, 1);
@@ -1023,7 +1278,7 @@ mma_batch_kernel(const MmaArgs* __restrict__ insts, const int2* __restrict__ wor
     const int w = *m.item;
     if (w >= nwork || *m.abort_flag) break;
     const int2 W = work[w];
-    run_tile<kMode, true>(insts[W.x], m, (long long)W.y * kTileM, rs);
+    run_tile<kMode, true, false>(insts[W.x], m, (long long)W.y * kTileM, rs, nullptr);
     __syncthreads();  // outputs written; per-row tables free for the next item
   }
   cta_teardown(m);
@@ -1306,19 +1561,50 @@ void set_acc_regions(MmaArgs& a, int npad_max) {
   a.acc_ovl = 2 * W - T;
 }
 
+// x^T: the transposed copy of x (D rows of ld floats, candidates inner),
+// with its TMA map; when given, the producers gather rows of it.
+struct XtView {
+  const float* xt = nullptr;
+  const CUtensorMap* map = nullptr;
+};
+
 template <int kMode>
 cudaError_t launch_mode(const MmaPlan& p, const Tables& tb, const Function& F, const float* x,
                         int N, float* out, cudaStream_t st, const int* list = nullptr,
                         int nlist = 0, double* gout = nullptr, double* d2out = nullptr,
-                        float* zbuf = nullptr) {
+                        float* zbuf = nullptr, XtView xv = XtView()) {
+  using C = MC<kMode>;
   const int npad_max = npad_of(F.max_n);
   const int ncmax = kMode == M_EXACT ? std::min(npad_max, kExactMaxNC) : npad_max;
   const size_t sb = stage_bytes_for<kMode>(ncmax);
   const size_t ctrl = ctrl_bytes();
   const int nstage = (int)std::min<size_t>(kMaxStages, (kSmemCap - ctrl) / sb);
   if (nstage < 2) return cudaErrorInvalidValue;
-  const size_t smem = nstage * sb + ctrl + 1024;  // + alignment slack
+  // heavy kinds in the epilogue only when there is no z scratch for them
+  const bool heavy = zbuf == nullptr && F.hcols > 0;
   MmaArgs a;
+  a.xt = 0;
+  a.nA = a.nB = nstage;
+  a.a_bytes = C::kParts * C::kPart;
+  a.b_bytes = (int)sb - a.a_bytes;
+  size_t smem = nstage * sb + ctrl + 1024;  // + alignment slack
+  if (xv.xt && !heavy) {
+    // separate rings: B slots hold a whole stage of R (the larger), A slots
+    // the candidates' operands with their raw gathers inside
+    const size_t ab = (size_t)C::kParts * C::kPart;
+    const size_t bb = (size_t)C::kParts * ncmax * C::kRow;
+    const int nB = kMode == M_EXACT ? 4 : 3;
+    const long long room = (long long)kSmemCap - (long long)ctrl - (long long)nB * bb;
+    const int nA = room > 0 ? (int)std::min<long long>(kMaxARing, room / (long long)ab) : 0;
+    if (nA >= 3) {
+      a.xt = 1;
+      a.nA = nA;
+      a.nB = nB;
+      a.a_bytes = (int)ab;
+      a.b_bytes = (int)bb;
+      smem = nA * ab + nB * bb + ctrl + 1024;
+    }
+  }
   a.tb = tb;
   a.F = F;
   a.x = x;
@@ -1337,14 +1623,73 @@ cudaError_t launch_mode(const MmaPlan& p, const Tables& tb, const Function& F, c
   a.d2out = d2out;
   a.zbuf = zbuf;
   set_acc_regions<kMode>(a, npad_max);
-  // heavy kinds in the epilogue only when there is no z scratch for them
-  const bool heavy = zbuf == nullptr && F.hcols > 0;
-  const auto kern = heavy ? mma_eval_kernel<kMode, true> : mma_eval_kernel<kMode, false>;
+  CUtensorMap none;
+  memset(&none, 0, sizeof(none));
+  const CUtensorMap& map = a.xt ? *xv.map : none;
+  const auto kern = a.xt ? mma_eval_kernel<kMode, false, true>
+                         : (heavy ? mma_eval_kernel<kMode, true, false>
+                                  : mma_eval_kernel<kMode, false, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)((N + kTileM - 1) / kTileM), kThreads, smem, st>>>(a);
+  kern<<<(unsigned)((N + kTileM - 1) / kTileM), a.xt ? kThreadsXT : kThreads, smem, st>>>(a, map);
   return cudaGetLastError();
 }
+
+// x (N x D, row-major) -> x^T (D rows of ld floats), zeros past N: 64 x 64
+// tiles through shared memory, read and written 16 bytes per thread and
+// access (both sides coalesced).  Needs D % 4 == 0 and 16-byte aligned x;
+// otherwise transpose_x_scalar_kernel.
+__global__ void __launch_bounds__(256) transpose_x_kernel(const float* __restrict__ x, int N,
+                                                          int D, float* __restrict__ xt, int ld) {
+  __shared__ float tile[64][65];
+  const int c0 = blockIdx.x * 64;  // variables
+  const int r0 = blockIdx.y * 64;  // candidates
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16
+  for (int k = ty; k < 64; k += 16) {
+    const int r = r0 + k, c = c0 + 4 * tx;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r < N && c < D) v = *reinterpret_cast<const float4*>(x + (size_t)r * D + c);
+    tile[k][4 * tx] = v.x;
+    tile[k][4 * tx + 1] = v.y;
+    tile[k][4 * tx + 2] = v.z;
+    tile[k][4 * tx + 3] = v.w;
+  }
+  __syncthreads();
+  for (int k = ty; k < 64; k += 16) {
+    const int c = c0 + k, r = r0 + 4 * tx;
+    if (c < D && r < ld)
+      *reinterpret_cast<float4*>(xt + (size_t)c * ld + r) =
+          make_float4(tile[4 * tx][k], tile[4 * tx + 1][k], tile[4 * tx + 2][k], tile[4 * tx + 3][k]);
+  }
+}
+__global__ void transpose_x_scalar_kernel(const float* __restrict__ x, int N, int D,
+                                          float* __restrict__ xt, int ld) {
+  __shared__ float tile[32][33];
+  const int c0 = blockIdx.x * 32;  // variables
+  const int r0 = blockIdx.y * 32;  // candidates
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int r = r0 + k, c = c0 + threadIdx.x;
+    tile[k][threadIdx.x] = (r < N && c < D) ? x[(size_t)r * D + c] : 0.f;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int c = c0 + k, r = r0 + threadIdx.x;
+    if (c < D && r < ld) xt[(size_t)c * ld + r] = tile[threadIdx.x][k];
+  }
+}
+
+cudaError_t launch_transpose_x(const float* x, int n, int D, float* xt, int ld, cudaStream_t st) {
+  if ((D & 3) == 0 && (reinterpret_cast<uintptr_t>(x) & 15u) == 0 && (ld & 3) == 0)
+    transpose_x_kernel<<<dim3((D + 63) / 64, (unsigned)((ld + 63) / 64)), 256, 0, st>>>(x, n, D,
+                                                                                     xt, ld);
+  else
+    transpose_x_scalar_kernel<<<dim3((D + 31) / 32, (unsigned)((ld + 31) / 32)), dim3(32, 8), 0,
+                                st>>>(x, n, D, xt, ld);
+  return cudaGetLastError();
+}
+
+// Candidates per row of x^T, rounded so that the rows start 128 bytes apart.
+inline int xt_ld(int n) { return (n + 31) / 32 * 32; }
 
 }  // namespace
 
@@ -1505,6 +1850,10 @@ void mma_fill_args(void* dst, const MmaPlan& p, const Tables& tb, const Function
   a.onat = p.onat;
   a.nstage = g.nstage;
   a.stage_bytes = g.stage_bytes;
+  a.xt = 0;
+  a.nA = a.nB = g.nstage;
+  a.a_bytes = MC<M_EXACT>::kParts * MC<M_EXACT>::kPart;
+  a.b_bytes = g.stage_bytes - a.a_bytes;
   a.nlist = F.ncomp;
   for (int i = 0; i < kMaxComponents; ++i) a.list[i] = i;
   a.gout = nullptr;
@@ -1538,14 +1887,15 @@ namespace {
 // components `list` (all of F's when nullptr).
 cudaError_t launch_any(int mode, const MmaPlan& p, const Tables& tb, const Function& F,
                        const float* x, int N, float* out, cudaStream_t st, const int* list,
-                       int nlist, double* gout, double* d2out, float* zbuf) {
+                       int nlist, double* gout, double* d2out, float* zbuf,
+                       XtView xv = XtView()) {
   switch (mode) {
     case CUROB_PRECISION_TF32X3:
-      return launch_mode<M_TF32>(p, tb, F, x, N, out, st, list, nlist, gout, d2out, zbuf);
+      return launch_mode<M_TF32>(p, tb, F, x, N, out, st, list, nlist, gout, d2out, zbuf, xv);
     case CUROB_PRECISION_BF16X3:
-      return launch_mode<M_BF16>(p, tb, F, x, N, out, st, list, nlist, gout, d2out, zbuf);
+      return launch_mode<M_BF16>(p, tb, F, x, N, out, st, list, nlist, gout, d2out, zbuf, xv);
     case CUROB_PRECISION_EXACT:
-      return launch_mode<M_EXACT>(p, tb, F, x, N, out, st, list, nlist, gout, d2out, zbuf);
+      return launch_mode<M_EXACT>(p, tb, F, x, N, out, st, list, nlist, gout, d2out, zbuf, xv);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1581,28 +1931,65 @@ cudaError_t launch_split(const MmaPlan& p, const Tables& tb, const Function& F, 
                          const float* x, int N, float* out, cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
   const SplitPlan sp = split_plan(F, cmode, N);
-  if (sp.direct)
-    return launch_any(sp.mode[0], p, tb, F, x, N, out, st, nullptr, 0, nullptr, nullptr, nullptr);
+  const int D = tb.D;
+  // Each slice of x is first transposed (x^T, D rows of ld candidates), so
+  // that the producers fetch a K stage's variables as TMA row gathers; the
+  // copy shares the stream-ordered scratch.  Without room for it the
+  // producers gather from x itself.
+  const int ld = xt_ld((int)sp.rows);
+  bool use_xt = (ld + 31) / 32 <= 65535 && (N + kTileM - 1) / kTileM >= 1;
+  const size_t scratch = sp.direct ? 0 : sp.per_row * (size_t)sp.rows;
+  const size_t off_xt = (scratch + 255) / 256 * 256;
   void* buf = nullptr;
-  const size_t bytes = sp.per_row * (size_t)sp.rows;
-  cudaError_t e = p.pool ? cudaMallocFromPoolAsync(&buf, bytes, p.pool, st)
-                         : cudaMallocAsync(&buf, bytes, st);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    if (sp.ngroups == 1)  // no room: the epilogue evaluates the heavy kinds itself
-      return launch_any(sp.mode[0], p, tb, F, x, N, out, st, nullptr, 0, nullptr, nullptr,
-                        nullptr);
-    return e;
+  cudaError_t e = cudaErrorMemoryAllocation;
+  auto alloc = [&](size_t bytes) {
+    e = p.pool ? cudaMallocFromPoolAsync(&buf, bytes, p.pool, st) : cudaMallocAsync(&buf, bytes, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      buf = nullptr;
+    }
+  };
+  if (use_xt) alloc(off_xt + (size_t)D * ld * sizeof(float));
+  if (!buf) {
+    use_xt = false;
+    if (sp.direct)
+      return launch_any(sp.mode[0], p, tb, F, x, N, out, st, nullptr, 0, nullptr, nullptr, nullptr);
+    alloc(scratch);
+    if (!buf) {
+      if (sp.ngroups == 1)  // no room: the epilogue evaluates the heavy kinds itself
+        return launch_any(sp.mode[0], p, tb, F, x, N, out, st, nullptr, 0, nullptr, nullptr,
+                          nullptr);
+      return e;
+    }
   }
+  e = cudaSuccess;
+  float* xtp = use_xt ? reinterpret_cast<float*>(static_cast<char*>(buf) + off_xt) : nullptr;
   for (long long r0 = 0; r0 < N && e == cudaSuccess; r0 += sp.rows) {
     const int n = (int)std::min<long long>(sp.rows, N - r0);
+    const float* xs = x + (size_t)r0 * D;
+    XtView xv;
+    CUtensorMap map;
+    if (use_xt) {
+      e = launch_transpose_x(xs, n, D, xtp, ld, st);
+      if (e == cudaSuccess &&
+          encode_2d(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, xtp, (uint64_t)n, (uint64_t)D,
+                    (uint64_t)ld * sizeof(float), kTileM, 1, CU_TENSOR_MAP_SWIZZLE_NONE)) {
+        xv.xt = xtp;
+        xv.map = &map;
+      }
+    }
+    if (sp.direct) {
+      if (e == cudaSuccess)
+        e = launch_any(sp.mode[0], p, tb, F, xs, n, out + r0, st, nullptr, 0, nullptr, nullptr,
+                       nullptr, xv);
+      continue;
+    }
     double* g = static_cast<double*>(buf);
     double* d2 = g + (size_t)kMaxComponents * n;
     float* z = F.hcols > 0 ? reinterpret_cast<float*>(d2 + (size_t)kMaxComponents * n) : nullptr;
-    const float* xs = x + (size_t)r0 * tb.D;
     for (int gi = 0; gi < sp.ngroups && e == cudaSuccess; ++gi)
       e = launch_any(sp.mode[gi], p, tb, F, xs, n, out + r0, st, sp.list[gi], sp.nlist[gi], g,
-                     d2, z);
+                     d2, z, xv);
     if (e == cudaSuccess) {
       finish_kernel<<<(unsigned)((n + kFinX - 1) / kFinX), dim3(kFinX, kFinSlices), 0, st>>>(
           tb, F, z, g, d2, n, out + r0);
@@ -1626,9 +2013,10 @@ int mma_launch_count(const Function& F, int mode, int N) {
   int cmode[kMaxComponents];
   component_modes(F, mode, cmode);
   const SplitPlan sp = split_plan(F, cmode, N);
-  if (sp.direct) return 1;
   const long long slices = (N + sp.rows - 1) / sp.rows;
-  return (int)(slices * (sp.ngroups + 1));
+  // per slice: the transpose of x, one launch per precision group, and the
+  // finish kernel unless one launch writes f itself
+  return (int)(slices * (1 + sp.ngroups + (sp.direct ? 0 : 1)));
 }
 
 cudaError_t launch_mma_fused(const MmaPlan& p, const Tables& tb, const Function& F, int mode,

@@ -63,7 +63,8 @@ def test_noalloc_matches_evaluatef_twice(orc, torch_cuda):
         auto = _reference(cu, torch, fids, xs, cu.PRECISION_AUTO)
         exact = _reference(cu, torch, fids, xs, cu.PRECISION_EXACT)
         cu.curob_set_precision(cu.PRECISION_EXACT)
-        fused = [cu.curob_query_launches(fid, n) == 1 for fid, n in zip(fids, Ns)]
+        # one tensor-core launch (after the transpose of x), no finish kernel
+        fused = [cu.curob_query_launches(fid, n) <= 2 for fid, n in zip(fids, Ns)]
         cu.curob_set_precision(cu.PRECISION_AUTO)
         assert not all(fused) and any(fused)  # both kinds of item are covered
         for fid, x, o, a, e, one in zip(fids, xs, outs, auto, exact, fused):
