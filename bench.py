@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="curob", choices=["curob", "reference"])
     ap.add_argument("--precision", default="auto",
-                    choices=["auto", "tf32x3", "bf16x3", "simt", "exact"])
+                    choices=["auto", "tf32x3", "bf16x3", "simt", "exact", "fp16x3"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
@@ -250,7 +250,7 @@ def roofline(cu, pk, src, modes, launch_ms, launches, args):
     members' precisions reach."""
     bf16 = pk["bf16_tflops"]
     clk = pk.get("sm_max_mhz", 2070.0) * 1e6
-    mode_peak = {1: bf16 * TF32_OVER_BF16 / 3.0, 2: bf16 / 3.0, 4: bf16 / 10.0,
+    mode_peak = {1: bf16 * TF32_OVER_BF16 / 3.0, 2: bf16 / 3.0, 4: bf16 / 10.0, 6: bf16 / 3.0,
                  3: SMS * FP32_PER_CLK * 2 * clk / 1e12 / 6.0}
     sfu_rate = SMS * SFU_PER_CLK * clk
     alu_rate = SMS * FP32_PER_CLK * clk
@@ -297,9 +297,10 @@ def roofline(cu, pk, src, modes, launch_ms, launches, args):
     names = {1: "mma_eval_kernel<TF32X3> (+ finish_kernel for heavy kinds)",
              2: "mma_eval_kernel<BF16X3> (+ finish_kernel for heavy kinds)",
              4: "mma_eval_kernel<EXACT> (+ finish_kernel for heavy kinds)",
+             6: "mma_eval_kernel<FP16X3> (+ finish_kernel for heavy kinds)",
              3: "eval_simt_f32_kernel",
              5: "mma_eval_kernel<EXACT> + <TF32X3> + finish_kernel (mixed compositions)"}
-    group = {1: "tf32x3", 2: "bf16x3", 4: "exact", 3: "simt", 5: "mixed"}[dom]
+    group = {1: "tf32x3", 2: "bf16x3", 4: "exact", 3: "simt", 5: "mixed", 6: "fp16x3"}[dom]
     table, sha = _profile_traffic()
     traffic = table.get(group) if (table and args.precision == "auto") else None
     roof = {"bound": "tensor" if dom != 3 else "alu", "kernel": names[dom],
@@ -309,6 +310,7 @@ def roofline(cu, pk, src, modes, launch_ms, launches, args):
             "traffic_kernel_sources_sha256_16": sha,
             "algorithmic_bytes_per_call": (4 * D + 4) * N,
             "peak_source": f"{src} bf16 burst; per algorithmic product: EXACT / 10 BF16 products, "
+                           "FP16X3 / 3 FP16 products (FP16 and BF16 share the dense rate), "
                            "TF32X3 x 1.1/2.25 (TF32/BF16 dense, nominal) / 3 TF32 products",
             "share_of_step": round(share[dom] / launch_ms.sum(), 3),
             "launches_per_step": int(np.array(launches)[sel].sum()),
@@ -354,7 +356,7 @@ def run_curob(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     cu.curob_initialize(D, N, SEED)
-    mode = {"auto": 0, "tf32x3": 1, "bf16x3": 2, "simt": 3, "exact": 4}[args.precision]
+    mode = {"auto": 0, "tf32x3": 1, "bf16x3": 2, "simt": 3, "exact": 4, "fp16x3": 6}[args.precision]
     cu.curob_set_precision(mode)
 
     # 37 FP32 batches, resident in HBM before timing starts (one for a
@@ -487,9 +489,9 @@ def run_curob(args):
         # function at this size (GPU parity tests): TF32X3 and BF16X3 do not
         # on the functions that magnify contraction error, which AUTO routes
         # to EXACT
-        meets = {"tf32x3": False, "bf16x3": False, "exact": True, "simt": True}
+        meets = {"tf32x3": False, "bf16x3": False, "fp16x3": False, "exact": True, "simt": True}
         forced = {}
-        for name, m in (("tf32x3", 1), ("bf16x3", 2), ("exact", 4), ("simt", 3)):
+        for name, m in (("tf32x3", 1), ("bf16x3", 2), ("fp16x3", 6), ("exact", 4), ("simt", 3)):
             forced[name] = {"evals_s": round(NFUN * N / (timed_pass(m) / 1e3), 1),
                             "meets_fp32_tolerance_on_all_functions": meets[name]}
         extra["forced_precision"] = forced
@@ -584,8 +586,8 @@ def run_curob(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 in/out; rotation on tensor cores as tf32x3 (3 TF32 products) or exact "
-                     "(BF16 integer slices), per function and member (auto); double-float "
-                     "shift; FP64 sums", "data": "synthetic",
+                     "(BF16 integer slices), per function and member (auto); FP64 sums",
+            "data": "synthetic",
             "config": {"workload": f"37 functions x N={N} candidates U[-100,100]^{D}, FP32",
                        "D": D, "N": N, "functions": NFUN, "precision": args.precision,
                        "l2": "37 distinct input batches (2.4 GB) > L2 per step",
@@ -600,7 +602,7 @@ def run_curob(args):
             **extra,
             "per_function_ms": [round(v, 4) for v in launch_ms.tolist()],
             "per_function_path": [{1: "tf32x3", 2: "bf16x3", 3: "simt", 4: "exact",
-                                   5: "mixed"}[m] for m in modes],
+                                   5: "mixed", 6: "fp16x3"}[m] for m in modes],
             "per_function_launches": launches,
             "roofline": roof, "roofline_per_function": per_fn, "cpu_baseline": cpu, "e2e": e2e, "ragged_batch": ragged,
             "surrogate": surrogate, "small_batch": small,

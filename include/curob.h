@@ -60,6 +60,10 @@ typedef enum {
  * accumulated exactly (every partial sum an integer below 2^23), the nine
  * lower-weight products in a second FP32 accumulator 2^-8 below it; z to
  * about 2^-26 of each candidate's |x - o|_max.
+ * FP16X3: y scaled by a power of two above each candidate's max |x - o|
+ * over the component and R by a power of two per row, both cut into FP16
+ * hi + lo (22 significant bits, as TF32 hi + lo), three products with FP32
+ * accumulation at the FP16 tensor rate (half the operand bytes of TF32X3).
  * SIMT: FP32 CUDA cores with a compensated dot product.  AUTO (default):
  * EXACT for functions containing Discus, Weierstrass, expanded
  * Griewank-Rosenbrock or Katsuura (they magnify z errors), TF32X3 for the
@@ -73,7 +77,8 @@ typedef enum {
   CUROB_PRECISION_BF16X3 = 2,
   CUROB_PRECISION_SIMT = 3,
   CUROB_PRECISION_EXACT = 4,
-  CUROB_PRECISION_MIXED = 5
+  CUROB_PRECISION_MIXED = 5,
+  CUROB_PRECISION_FP16X3 = 6
 } curob_precision;
 
 /* Number of functions (Table 1). */
@@ -130,7 +135,8 @@ curob_status curob_evaluatef(int fid, const float* x, int N, float* out, curob_s
 curob_status curob_h_evaluate(int fid, const double* x, int N, double* out);
 curob_status curob_h_evaluatef(int fid, const float* x, int N, float* out);
 
-/* Select the precision of curob_evaluatef (see curob_precision). */
+/* Select the precision of curob_evaluatef (see curob_precision; every value
+ * but MIXED; INVALID_ARGUMENT otherwise). */
 curob_status curob_set_precision(int mode);
 
 /* Small populations (the paper's timing setting, Sec. 2: 50 candidates per

@@ -22,6 +22,7 @@ CODES = {v: k for k, v in STATUS.items()}
 
 PRECISION_AUTO, PRECISION_TF32X3, PRECISION_BF16X3, PRECISION_SIMT, PRECISION_EXACT = 0, 1, 2, 3, 4
 PRECISION_MIXED = 5  # reported for compositions whose members take different precisions
+PRECISION_FP16X3 = 6
 NUM_FUNCTIONS = 37
 FOPT = 100.0
 

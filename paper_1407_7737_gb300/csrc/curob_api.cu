@@ -111,7 +111,7 @@ int resolve_precision(const Function& F) {
   int mode = g.precision;
   const bool mma_ok = mma_supports(g.inst.mma, F);
   const bool tc = mode == CUROB_PRECISION_TF32X3 || mode == CUROB_PRECISION_BF16X3 ||
-                  mode == CUROB_PRECISION_EXACT;
+                  mode == CUROB_PRECISION_EXACT || mode == CUROB_PRECISION_FP16X3;
   if (tc && !mma_ok) return -1;
   if (mode == CUROB_PRECISION_AUTO)
     mode = mma_ok ? mma_auto_mode(g.inst.mma, F) : CUROB_PRECISION_SIMT;
@@ -286,7 +286,8 @@ curob_status curob_h_evaluatef(int fid, const float* x, int N, float* out) {
 }
 
 curob_status curob_set_precision(int mode) {
-  if (mode < CUROB_PRECISION_AUTO || mode > CUROB_PRECISION_EXACT)
+  if (mode < CUROB_PRECISION_AUTO || mode > CUROB_PRECISION_FP16X3 ||
+      mode == CUROB_PRECISION_MIXED)
     return CUROB_ERR_INVALID_ARGUMENT;
   g.precision = mode;
   return CUROB_OK;

@@ -55,6 +55,7 @@
 // DEV_TIMEOUT in the status word, the CTA stops, and TMEM is freed before
 // exit.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cstring>
@@ -85,7 +86,10 @@ constexpr size_t kSmemCap = 227 * 1024 - 1024;   // dynamic shared memory, less 
 constexpr int kExactAcc1 = 256;                  // EXACT: TMEM column of accumulator 1
 constexpr int kSigRing = 8;                      // EXACT: row scales in flight
 
-enum Mode : int { M_TF32 = 0, M_BF16 = 1, M_EXACT = 2 };
+enum Mode : int { M_TF32 = 0, M_BF16 = 1, M_EXACT = 2, M_F16 = 3 };
+// Modes whose operands are scaled per row: y by sigma_m (a power of two above
+// the candidate's max_j |x_j - o_j| over the component), R by tau_i.
+__host__ __device__ constexpr bool scaled_mode(int m) { return m == M_EXACT || m == M_F16; }
 
 // EXACT splits a block's npad output columns into nchunk equal chunks of at
 // most kExactMaxNC (a multiple of 16 wide): accumulators 0 and 1 of a chunk
@@ -115,10 +119,10 @@ __device__ __forceinline__ void shift_ff(float x, float ohi, float olo, float& y
 // that its four operand parts still leave room for five stages.
 template <int kMode> struct MC {
   static constexpr int kParts = kMode == M_EXACT ? 4 : 2;  // A/B operand parts
-  static constexpr int kKs = kMode == M_BF16 ? 32 : 16;    // K columns per stage
+  static constexpr int kKs = (kMode == M_BF16 || kMode == M_F16) ? 32 : 16;  // K per stage
   static constexpr int kEl = kMode == M_TF32 ? 4 : 2;      // bytes per element
   static constexpr int kMmaK = kMode == M_TF32 ? 8 : 16;   // K per MMA
-  static constexpr uint32_t kFmt = kMode == M_TF32 ? 2u : 1u;
+  static constexpr uint32_t kFmt = kMode == M_TF32 ? 2u : (kMode == M_F16 ? 0u : 1u);
   static constexpr int kRow = kMode == M_EXACT ? 32 : 64;  // bytes of a part's row
   static constexpr int kPart = kTileM * kRow;              // bytes of an A part
 };
@@ -170,7 +174,7 @@ struct MmaArgs {
 static_assert(sizeof(MmaArgs) <= 512, "MmaArgs outgrew the allocation-free argument area");
 
 // Floats reserved per block for each precision's image (the TF32 size; BF16
-// needs half).  A block's images: [TF32][BF16][EXACT].
+// and FP16 need half).  A block's images: [TF32][BF16][EXACT][FP16].
 __host__ __device__ inline long long image_floats(int npad) { return 2LL * npad * npad; }
 
 // ------------------------------------------------------- epilogue helpers
@@ -563,8 +567,10 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
       const float* ohi = a.ohi + Cm.base;
       const float* olo = a.olo + Cm.base;
       double d2 = 0.0;
+      // ||x - o||^2 only feeds the composition weights
+      const bool need_d2 = F.composition != 0 || a.d2out != nullptr;
       float isig = 1.f;
-      if constexpr (kMode == M_EXACT) {
+      if constexpr (scaled_mode(kMode)) {
         // max_j |x_j - o_j| of each row over the component, read in natural
         // order: half h of the warp pair reads rows 16 h .. 16 h + 15 of the
         // pair's 32 with coalesced loads (o as FP32); the maxima meet in
@@ -602,7 +608,7 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
         // stage the block's index list and o words in shared memory (the
         // previous block's readers are done at the first barrier)
         if (!producers_sync(prod_bar, pphase, abort_flag, tb.status)) { ok = false; break; }
-        if constexpr (kMode == M_EXACT) {
+        if constexpr (scaled_mode(kMode)) {
           if (si == 0) {  // row scale sigma_m = 2^e > the row's maximum
             const float mx = m.rowMx[r];
             int e = 0;
@@ -684,8 +690,17 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
               // branch-free, so that the chunk's elements interleave.  A
               // column past the block has x = 0 (zero-filled copy) and o = 0
               // (staged), so y = 0; a row past the batch is never written.
-              shift_ff(xv[cc * kPer + e], oh[e], ol[e], yh[e], yl[e]);
-              d2p = fmaf(yh[e], yh[e], d2p);
+              // EXACT slices y to 2^-26 of the row scale: the exact
+              // double-float shift.  The split modes keep 22 (16) bits of y:
+              // x - o_hi is exact near o (Sterbenz) and one more rounding of
+              // the low word of o stays below those bits.
+              if constexpr (kMode == M_EXACT) {
+                shift_ff(xv[cc * kPer + e], oh[e], ol[e], yh[e], yl[e]);
+              } else {
+                yh[e] = __fsub_rn(__fsub_rn(xv[cc * kPer + e], oh[e]), ol[e]);
+                yl[e] = 0.f;
+              }
+              if (need_d2) d2p = fmaf(yh[e], yh[e], d2p);
             }
             const uint32_t off = swz_m<kMode>((uint32_t)r, (uint32_t)(c * 16));
             if constexpr (kMode == M_TF32) {
@@ -707,6 +722,23 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
                 hw[qq] = pack_bf16(a, b);
                 const float2 hf = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&hw[qq]));
                 lw[qq] = pack_bf16((a - hf.x) + yl[2 * qq], (b - hf.y) + yl[2 * qq + 1]);
+              }
+              *reinterpret_cast<uint4*>(A + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+              *reinterpret_cast<uint4*>(A + kPart + off) =
+                  make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            } else if constexpr (kMode == M_F16) {
+              // y / sigma in (-1, 1) (an exact power-of-two scaling) as FP16
+              // hi + lo: 22 significant bits, as TF32 hi + lo
+              uint32_t hw[4], lw[4];
+#pragma unroll
+              for (int qq = 0; qq < 4; ++qq) {
+                const float a = yh[2 * qq] * isig, b = yh[2 * qq + 1] * isig;
+                const __half2 hh = __floats2half2_rn(a, b);
+                const float2 hf = __half22float2(hh);
+                const __half2 ll = __floats2half2_rn(fmaf(yl[2 * qq], isig, a - hf.x),
+                                                     fmaf(yl[2 * qq + 1], isig, b - hf.y));
+                hw[qq] = *reinterpret_cast<const uint32_t*>(&hh);
+                lw[qq] = *reinterpret_cast<const uint32_t*>(&ll);
               }
               *reinterpret_cast<uint4*>(A + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
               *reinterpret_cast<uint4*>(A + kPart + off) =
@@ -852,8 +884,17 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
               // branch-free, so that the chunk's elements interleave.  A
               // column past the block has x = 0 (zero-filled copy) and o = 0
               // (staged), so y = 0; a row past the batch is never written.
-              shift_ff(xv[cc * kPer + e], oh[e], ol[e], yh[e], yl[e]);
-              d2p = fmaf(yh[e], yh[e], d2p);
+              // EXACT slices y to 2^-26 of the row scale: the exact
+              // double-float shift.  The split modes keep 22 (16) bits of y:
+              // x - o_hi is exact near o (Sterbenz) and one more rounding of
+              // the low word of o stays below those bits.
+              if constexpr (kMode == M_EXACT) {
+                shift_ff(xv[cc * kPer + e], oh[e], ol[e], yh[e], yl[e]);
+              } else {
+                yh[e] = __fsub_rn(__fsub_rn(xv[cc * kPer + e], oh[e]), ol[e]);
+                yl[e] = 0.f;
+              }
+              if (need_d2) d2p = fmaf(yh[e], yh[e], d2p);
             }
             const uint32_t off = swz_m<kMode>((uint32_t)r, (uint32_t)(c * 16));
             if constexpr (kMode == M_TF32) {
@@ -875,6 +916,23 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
                 hw[qq] = pack_bf16(a, b);
                 const float2 hf = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&hw[qq]));
                 lw[qq] = pack_bf16((a - hf.x) + yl[2 * qq], (b - hf.y) + yl[2 * qq + 1]);
+              }
+              *reinterpret_cast<uint4*>(A + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+              *reinterpret_cast<uint4*>(A + kPart + off) =
+                  make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            } else if constexpr (kMode == M_F16) {
+              // y / sigma in (-1, 1) (an exact power-of-two scaling) as FP16
+              // hi + lo: 22 significant bits, as TF32 hi + lo
+              uint32_t hw[4], lw[4];
+#pragma unroll
+              for (int qq = 0; qq < 4; ++qq) {
+                const float a = yh[2 * qq] * isig, b = yh[2 * qq + 1] * isig;
+                const __half2 hh = __floats2half2_rn(a, b);
+                const float2 hf = __half22float2(hh);
+                const __half2 ll = __floats2half2_rn(fmaf(yl[2 * qq], isig, a - hf.x),
+                                                     fmaf(yl[2 * qq + 1], isig, b - hf.y));
+                hw[qq] = *reinterpret_cast<const uint32_t*>(&hh);
+                lw[qq] = *reinterpret_cast<const uint32_t*>(&ll);
               }
               *reinterpret_cast<uint4*>(A + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
               *reinterpret_cast<uint4*>(A + kPart + off) =
@@ -944,7 +1002,7 @@ __device__ void epilogue_tile(const MmaArgs& a, const Smem& m, long long row0, R
       const Component Cm = tb.comp[F.comp0 + ci];
       double gsum = 0.0;
       float sig = 1.f;
-      if constexpr (kMode == M_EXACT) {
+      if constexpr (scaled_mode(kMode)) {
         if (!mbar_wait(&sig_full[cg % kSigRing], (cg / kSigRing) & 1u, abort_flag, tb.status))
           break;
         sig = rowSig[(cg % kSigRing) * kTileM + r];
@@ -994,6 +1052,10 @@ __device__ void epilogue_tile(const MmaArgs& a, const Smem& m, long long row0, R
 #pragma unroll
                 for (int k = 0; k < 32; ++k)
                   v[k] = (k < cend) ? (v[k] + g1[k]) * (base * tau[c + k]) : 0.f;
+              } else if constexpr (kMode == M_F16) {
+                tmem_ld32(t_lane + ab + (uint32_t)l, v);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) v[k] = (k < cend) ? v[k] * (sig * tau[c + k]) : 0.f;
               } else {
                 tmem_ld32(t_lane + ab + (uint32_t)l, v);
               }
@@ -1341,6 +1403,17 @@ __global__ void build_image_kernel(const ImgJob* jobs, const double* R, uint8_t*
       const __nv_bfloat16 l = __double2bfloat16(v - (double)__bfloat162float(h));
       *reinterpret_cast<__nv_bfloat16*>(hi + off) = h;
       *reinterpret_cast<__nv_bfloat16*>(lo + off) = l;
+    }
+    {  // FP16: stage t = col / 32, hi = fp16(R / tau_row), lo = fp16(R / tau_row - hi)
+      const int t = col / 32, k = col % 32;
+      uint8_t* hi = base + (size_t)3 * fl * 4 + (size_t)t * (2 * npad * kRowBytes);
+      uint8_t* lo = hi + npad * kRowBytes;
+      const uint32_t off = swz64((uint32_t)row, (uint32_t)(k * 2));
+      const double w = v / (double)tau[J.tau_off + row];  // exact: tau is 2^f
+      const __half h = __double2half(w);
+      const __half l = __double2half(w - (double)__half2float(h));
+      *reinterpret_cast<__half*>(hi + off) = h;
+      *reinterpret_cast<__half*>(lo + off) = l;
     }
     {  // EXACT: chunk cc = row / nw, stage t = col / 16 (32-byte rows), four slices
       const int nw = exact_nw(npad);
@@ -1724,7 +1797,7 @@ curob_status mma_prepare(MmaPlan& p, std::vector<Segment>& segs, const Tables& t
       continue;
     }
     s.img_off = off;
-    off += 3 * image_floats(s.npad);
+    off += 4 * image_floats(s.npad);
     s.tau_off = toff;
     toff += s.npad;
   }
@@ -1896,6 +1969,8 @@ cudaError_t launch_any(int mode, const MmaPlan& p, const Tables& tb, const Funct
       return launch_mode<M_BF16>(p, tb, F, x, N, out, st, list, nlist, gout, d2out, zbuf, xv);
     case CUROB_PRECISION_EXACT:
       return launch_mode<M_EXACT>(p, tb, F, x, N, out, st, list, nlist, gout, d2out, zbuf, xv);
+    case CUROB_PRECISION_FP16X3:
+      return launch_mode<M_F16>(p, tb, F, x, N, out, st, list, nlist, gout, d2out, zbuf, xv);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -2035,7 +2110,7 @@ cudaError_t launch_mma_mixed(const MmaPlan& p, const Tables& tb, const Function&
 cudaError_t launch_mma(const MmaPlan& p, const Tables& tb, const Function& F, int mode,
                        const float* x, int N, float* out, cudaStream_t st) {
   if (mode != CUROB_PRECISION_TF32X3 && mode != CUROB_PRECISION_BF16X3 &&
-      mode != CUROB_PRECISION_EXACT)
+      mode != CUROB_PRECISION_EXACT && mode != CUROB_PRECISION_FP16X3)
     return cudaErrorInvalidValue;
   int cmode[kMaxComponents];
   component_modes(F, mode, cmode);

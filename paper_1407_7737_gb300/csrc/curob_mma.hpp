@@ -39,7 +39,7 @@ cudaError_t launch_mma_mixed(const MmaPlan& p, const Tables& tb, const Function&
 // One CTA whose wait on an mbarrier nothing completes runs out (2 s) and
 // writes DEV_TIMEOUT to *status.
 cudaError_t launch_wait_selftest(int* status, cudaStream_t st);
-// mode: CUROB_PRECISION_TF32X3, _BF16X3 or _EXACT.  A function with
+// mode: CUROB_PRECISION_TF32X3, _BF16X3, _FP16X3 or _EXACT.  A function with
 // heavy-kind blocks (kind_is_heavy) takes a second launch (finish kernel).
 cudaError_t launch_mma(const MmaPlan& p, const Tables& tb, const Function& F, int mode,
                        const float* x, int N, float* out, cudaStream_t st);

@@ -75,9 +75,9 @@ def test_auto_precision_parity_full_size(orc):
     assert not bad, bad
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 6])
 def test_forced_precisions_report(orc, mode):
-    """TF32x3 and BF16x3 forced on every function at D = 1000 (sampled rows):
+    """TF32x3, BF16x3 and FP16x3 forced on every function at D = 1000 (sampled rows):
     the per-function error ratio is recorded (AUTO routes the functions that
     magnify contraction error elsewhere); every value is finite."""
     D, N = 1000, 16384
