@@ -68,6 +68,8 @@ struct Function {
   int hcols;          // variables of the function's heavy-kind blocks (kind_is_heavy)
   int nseg;           // segments of all its components (consecutive in the table)
   int nweier;         // of them, Weierstrass blocks
+  int xcand;          // bit c: member c is unrotated and its kinds keep one sum
+                      // (kind_from_x): it can be evaluated straight from x
 };
 
 // Device view of an initialised instance.
@@ -156,6 +158,11 @@ __host__ __device__ constexpr bool kind_uses_a1(int k) {
 }
 __host__ __device__ constexpr bool kind_uses_a2(int k) { return k == K_LUNACEK || k == K_HGBAT; }
 __host__ __device__ constexpr bool kind_uses_p(int k) { return k == K_GRIEWANK || k == K_KATSUURA; }
+// Kinds whose terms feed one running sum only (no second sum, product or
+// neighbour pair): an unrotated block of such a kind needs no contraction.
+__host__ __device__ constexpr bool kind_from_x(int k) {
+  return !kind_uses_a1(k) && !kind_uses_a2(k) && !kind_uses_p(k) && !kind_has_pairs(k);
+}
 __host__ __device__ inline bool kind_is_sensitive(int k) {
   return k == K_DISCUS || k == K_WEIERSTRASS || k == K_EGR || k == K_KATSUURA;
 }

@@ -139,6 +139,7 @@ void Instance::build_tables() {
     F.hcols = 0;
     F.nseg = 0;
     F.nweier = 0;
+    F.xcand = 0;
     for (int c = 0; c < ci.n; ++c) {
       const Member& m = ci.m[c];
       CompHost ch;
@@ -203,6 +204,9 @@ void Instance::build_tables() {
         segs.push_back(s);
       }
       C.nseg = (int)segs.size() - C.seg0;
+      bool from_x = !m.rotated && C.nseg > 0;
+      for (int si = C.seg0; si < C.seg0 + C.nseg; ++si) from_x = from_x && kind_from_x(segs[si].kind);
+      if (from_x) F.xcand |= 1 << c;
       comps.push_back(C);
       chost.push_back(ch);
     }

@@ -1540,6 +1540,37 @@ static_assert(!kind_uses_a1(K_POWERS) && !kind_uses_a1(K_WEIERSTRASS) && !kind_u
                   !kind_uses_a2(K_SCHWEFEL) && !kind_uses_a2(K_KATSUURA) && !kind_uses_a2(K_SCHAFFER6),
               "heavy kinds use a0 and p only");
 
+// Members evaluated from x^T (Function::xcand): z_j = s y_j + c with y_j =
+// (x_j - o_hi,j) - o_lo,j, as the tensor-core path forms it for an identity
+// block; the slice's terms and its share of ||x - o||^2.
+template <int KIND>
+__device__ __forceinline__ void fin_terms_x(const float* xc, long long ld, const float* oh,
+                                            const float* ol, int j0, int j1, int gpos, float gn,
+                                            const float* aux, float kat_e, float s, float c0,
+                                            Acc<float>& acc, float& d2) {
+#pragma unroll 4
+  for (int j = j0; j < j1; ++j) {
+    const float y = __fsub_rn(__fsub_rn(xc[(long long)j * ld], oh[j]), ol[j]);
+    const float u = y * s;
+    elem_term_f32(KIND, u + c0, u, gpos + j, gn, aux ? aux[j] : 0.f, kat_e, acc);
+    d2 = fmaf(y, y, d2);
+  }
+}
+__device__ __forceinline__ void fin_dispatch_x(int kind, const float* xc, long long ld,
+                                               const float* oh, const float* ol, int j0, int j1,
+                                               int gpos, float gn, const float* aux, float kat_e,
+                                               float s, float c0, Acc<float>& acc, float& d2) {
+  switch (kind) {
+#define CUROB_FINX_CASE(K) \
+  case K: fin_terms_x<K>(xc, ld, oh, ol, j0, j1, gpos, gn, aux, kat_e, s, c0, acc, d2); break;
+    CUROB_FINX_CASE(K_SPHERE) CUROB_FINX_CASE(K_ELLIPSOID) CUROB_FINX_CASE(K_ELLIPTIC)
+    CUROB_FINX_CASE(K_POWERS) CUROB_FINX_CASE(K_STEP) CUROB_FINX_CASE(K_WEIERSTRASS)
+    CUROB_FINX_CASE(K_RASTRIGIN) CUROB_FINX_CASE(K_SCHWEFEL)
+#undef CUROB_FINX_CASE
+    default: break;
+  }
+}
+
 __device__ __forceinline__ void fin_warp_sum(double& a0, double& p) {
   // lanes tx, tx + kFinX, ... of a warp hold the same candidate
 #pragma unroll
@@ -1551,24 +1582,28 @@ __device__ __forceinline__ void fin_warp_sum(double& a0, double& p) {
 
 __global__ void __launch_bounds__(kFinX * kFinSlices, 8)
 finish_kernel(Tables tb, Function F, const float* zbuf, const double* gout, const double* d2out,
-              int N, float* out) {
+              int N, float* out, const float* xT, long long ld, const float* ohi,
+              const float* olo, uint32_t xmask) {
   constexpr int kWarps = kFinX * kFinSlices / 32;
   constexpr int kSlicesPerWarp = 32 / kFinX;
   __shared__ double red[2][kWarps][kFinX];
   __shared__ double Gs[kMaxComponents][kFinX];
+  __shared__ double D2s[kMaxComponents][kFinX];  // ||x - o_c||^2 of members read from x^T
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int warp = ty / kSlicesPerWarp;
   const long long i = (long long)blockIdx.x * kFinX + tx;
   const bool valid = i < N;
   const long long ic = valid ? i : 0;  // rows past N read row 0 and write nothing
   if (ty == 0)
-    for (int c = 0; c < F.ncomp; ++c) Gs[c][tx] = gout[(size_t)c * N + ic];
+    for (int c = 0; c < F.ncomp; ++c) Gs[c][tx] = (xmask >> c & 1u) ? 0.0 : gout[(size_t)c * N + ic];
   double a0 = 0.0, p = 1.0;
   for (int c = 0; c < F.ncomp; ++c) {
     const Component Cm = tb.comp[F.comp0 + c];
+    const bool fx = (xmask >> c & 1u) != 0;  // block-uniform
+    double d2acc = 0.0;
     for (int si = 0; si < Cm.nseg; ++si) {
       const Segment sg = tb.seg[Cm.seg0 + si];
-      if (sg.hoff < 0) continue;  // block-uniform: every thread takes the same path
+      if (!fx && sg.hoff < 0) continue;  // block-uniform: every thread takes the same path
       if (sg.gfirst) {
         a0 = 0.0;
         p = 1.0;
@@ -1576,9 +1611,17 @@ finish_kernel(Tables tb, Function F, const float* zbuf, const double* gout, cons
       const int L = (sg.n + kFinSlices - 1) / kFinSlices;
       const int j0 = min(sg.n, ty * L), j1 = min(sg.n, j0 + L);
       const float* aux = sg.aux_off >= 0 ? tb.aux32 + sg.aux_off : nullptr;
-      const float* zc = zbuf + (size_t)sg.hoff * N + ic;
       Acc<float> acc = acc_zero<float>();
-      fin_dispatch(sg.kind, zc, N, j0, j1, sg.gpos, (float)sg.gn, aux, sg.kat_e, acc);
+      if (fx) {
+        float d2f = 0.f;
+        fin_dispatch_x(sg.kind, xT + (size_t)sg.zoff * ld + ic, ld, ohi + Cm.base + sg.zoff,
+                       olo + Cm.base + sg.zoff, j0, j1, sg.gpos, (float)sg.gn, aux, sg.kat_e,
+                       (float)sg.scale, (float)sg.offset, acc, d2f);
+        d2acc += (double)d2f;
+      } else {
+        const float* zc = zbuf + (size_t)sg.hoff * N + ic;
+        fin_dispatch(sg.kind, zc, N, j0, j1, sg.gpos, (float)sg.gn, aux, sg.kat_e, acc);
+      }
       a0 += (double)acc.a0;
       if (kind_uses_p(sg.kind)) p *= (double)acc.p;
       if (sg.glast) {
@@ -1607,6 +1650,20 @@ finish_kernel(Tables tb, Function F, const float* zbuf, const double* gout, cons
         __syncthreads();
       }
     }
+    if (fx && F.composition) {  // the member's ||x - o||^2 across the slices
+      double one = 1.0;
+      fin_warp_sum(d2acc, one);
+      if (ty % kSlicesPerWarp == 0) red[0][warp][tx] = d2acc;
+      __syncthreads();
+      if (warp == 0) {
+        const int q = ty % kSlicesPerWarp;
+        double s0 = 0.0, pp = 1.0;
+        for (int w = q; w < kWarps; w += kSlicesPerWarp) s0 += red[0][w][tx];
+        fin_warp_sum(s0, pp);
+        if (ty == 0) D2s[c][tx] = s0;
+      }
+      __syncthreads();
+    }
   }
   if (ty != 0 || !valid) return;
   double f;
@@ -1614,7 +1671,7 @@ finish_kernel(Tables tb, Function F, const float* zbuf, const double* gout, cons
     double G[kMaxComponents], d2v[kMaxComponents];
     for (int c = 0; c < F.ncomp; ++c) {
       G[c] = Gs[c][tx];
-      d2v[c] = d2out[(size_t)c * N + i];
+      d2v[c] = (xmask >> c & 1u) ? D2s[c][tx] : d2out[(size_t)c * N + i];
     }
     f = compose(tb.comp + F.comp0, F.ncomp, G, d2v, tb.D);
   } else {
@@ -1977,21 +2034,28 @@ cudaError_t launch_any(int mode, const MmaPlan& p, const Tables& tb, const Funct
 
 struct SplitPlan {
   int ngroups = 0, mode[2] = {-1, -1}, list[2][kMaxComponents], nlist[2] = {0, 0};
+  uint32_t xmask = 0;      // members the finish kernel evaluates from x^T
   bool direct = false;     // one launch straight to f: no scratch, no finish kernel
   long long rows = 0;      // candidates per slice
   size_t per_row = 0;      // scratch bytes per candidate
 };
 
-// Groups F's components by precision (cmode[c]) in component order.
-SplitPlan split_plan(const Function& F, const int* cmode, int N) {
+// Groups F's components by precision (cmode[c]) in component order.  With
+// x^T at hand (with_xt), an unrotated member whose blocks' kinds keep a
+// single sum needs no contraction: the finish kernel evaluates it from x^T.
+SplitPlan split_plan(const Function& F, const int* cmode, int N, bool with_xt) {
   SplitPlan sp;
   for (int c = 0; c < F.ncomp; ++c) {
+    if (with_xt && (F.xcand >> c & 1)) {
+      sp.xmask |= 1u << c;
+      continue;
+    }
     const int g = (sp.ngroups == 0 || sp.mode[0] == cmode[c]) ? 0 : 1;
     if (g + 1 > sp.ngroups) sp.ngroups = g + 1;
     sp.mode[g] = cmode[c];
     sp.list[g][sp.nlist[g]++] = c;
   }
-  sp.direct = sp.ngroups == 1 && F.hcols == 0;
+  sp.direct = sp.ngroups == 1 && F.hcols == 0 && sp.xmask == 0;
   sp.per_row = sizeof(float) * (size_t)F.hcols + 2 * sizeof(double) * kMaxComponents;
   long long rows = (long long)(kScratchCap / sp.per_row) / kTileM * kTileM;
   sp.rows = std::min<long long>(std::max<long long>(rows, kTileM), std::max(N, 1));
@@ -2005,7 +2069,7 @@ SplitPlan split_plan(const Function& F, const int* cmode, int N) {
 cudaError_t launch_split(const MmaPlan& p, const Tables& tb, const Function& F, const int* cmode,
                          const float* x, int N, float* out, cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
-  const SplitPlan sp = split_plan(F, cmode, N);
+  SplitPlan sp = split_plan(F, cmode, N, true);
   const int D = tb.D;
   // Each slice of x is first transposed (x^T, D rows of ld candidates), so
   // that the producers fetch a K stage's variables as TMA row gathers; the
@@ -2027,6 +2091,7 @@ cudaError_t launch_split(const MmaPlan& p, const Tables& tb, const Function& F, 
   if (use_xt) alloc(off_xt + (size_t)D * ld * sizeof(float));
   if (!buf) {
     use_xt = false;
+    sp = split_plan(F, cmode, N, false);  // every member through the contraction
     if (sp.direct)
       return launch_any(sp.mode[0], p, tb, F, x, N, out, st, nullptr, 0, nullptr, nullptr, nullptr);
     alloc(scratch);
@@ -2067,7 +2132,8 @@ cudaError_t launch_split(const MmaPlan& p, const Tables& tb, const Function& F, 
                      d2, z, xv);
     if (e == cudaSuccess) {
       finish_kernel<<<(unsigned)((n + kFinX - 1) / kFinX), dim3(kFinX, kFinSlices), 0, st>>>(
-          tb, F, z, g, d2, n, out + r0);
+          tb, F, z, g, d2, n, out + r0, xtp, (long long)ld, p.ohi, p.olo,
+          use_xt ? sp.xmask : 0u);
       e = cudaGetLastError();
     }
   }
@@ -2087,7 +2153,7 @@ int mma_launch_count(const Function& F, int mode, int N) {
   if (N <= 0) return 0;
   int cmode[kMaxComponents];
   component_modes(F, mode, cmode);
-  const SplitPlan sp = split_plan(F, cmode, N);
+  const SplitPlan sp = split_plan(F, cmode, N, true);
   const long long slices = (N + sp.rows - 1) / sp.rows;
   // per slice: the transpose of x, one launch per precision group, and the
   // finish kernel unless one launch writes f itself
