@@ -234,6 +234,37 @@ def _profile_traffic():
     return (table if sha == want else None), want
 
 
+def fp64_summary(cu, N, per_path):
+    """curob_evaluate's two paths at the bench workload; the tensor-core
+    path's executed BF16 products (28 per algorithmic multiply-add of the
+    block rotations) over the whole call time, against the measured BF16
+    peak."""
+    pk, src = peaks()
+    t_ms, s_ms = per_path["tensor"], per_path["simt"]
+    prod = 0.0
+    for f in range(len(t_ms)):
+        for c in range(cu.curob_num_components(f)):
+            sizes, rot = cu.curob_component_layout(f, c)
+            if rot:
+                prod += 28 * 2.0 * sum(n * n for n in sizes) * N
+    achieved = prod / (sum(t_ms) / 1e3) / 1e12
+    peak = pk.get("bf16_tflops")
+    return {
+        "path": "tensor (AUTO): seven BF16 digits per operand, 28 products, exact class sums, "
+                "z rounded once; terms and sums in FP64",
+        "tensor_evals_s": round(len(t_ms) * N / (sum(t_ms) / 1e3), 1),
+        "simt_evals_s": round(len(s_ms) * N / (sum(s_ms) / 1e3), 1),
+        "speedup_vs_simt": round(sum(s_ms) / sum(t_ms), 2),
+        "per_function_ms_tensor": [round(v, 4) for v in t_ms],
+        "per_function_ms_simt": [round(v, 4) for v in s_ms],
+        "launches_per_call": [cu.curob_query_launches64(f, N) for f in range(len(t_ms))],
+        "bf16_products_tflops_over_call_time": round(achieved, 1),
+        "bf16_peak_tflops": peak,
+        "frac_of_bf16_peak": round(achieved / peak, 4) if peak else None,
+        "peak_source": src,
+    }
+
+
 def roofline(cu, pk, src, modes, launch_ms, launches, args):
     """Per-function binding roofline and the dominant group's tensor line.
 
@@ -495,21 +526,28 @@ def run_curob(args):
             forced[name] = {"evals_s": round(NFUN * N / (timed_pass(m) / 1e3), 1),
                             "meets_fp32_tolerance_on_all_functions": meets[name]}
         extra["forced_precision"] = forced
-        # FP64 path on the same workload (FP64 copy of the batches)
+        # FP64 path (curob_evaluate) on the same workload, FP64 copies of the
+        # batches: the tensor-core path (AUTO) and the FP64-pipe path
         x64 = torch.empty((N, D), dtype=torch.float64, device=dev)
         o64 = torch.empty(N, dtype=torch.float64, device=dev)
-        fp64_ms = 0.0
-        for fid in range(NFUN):
-            x64.copy_(X[fid])
-            cu.curob_evaluate(fid, x64, N, o64, stream)  # warm
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            cu.curob_evaluate(fid, x64, N, o64, stream)
-            b.record(stream)
-            torch.cuda.synchronize()
-            fp64_ms += a.elapsed_time(b)
-        fp64 = NFUN * N / (fp64_ms / 1e3)
+        per_path = {}
+        for name, pm in (("tensor", 2), ("simt", 1)):
+            cu.curob_set_precision64(pm)
+            ms = []
+            for fid in range(NFUN):
+                x64.copy_(X[fid])
+                cu.curob_evaluate(fid, x64, N, o64, stream)  # warm
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                cu.curob_evaluate(fid, x64, N, o64, stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            per_path[name] = ms
+        cu.curob_set_precision64(0)
+        fp64 = NFUN * N / (sum(per_path["tensor"]) / 1e3)
+        extra["fp64"] = fp64_summary(cu, N, per_path)
 
     ragged = None
     if rank == 0 and not args.no_extra:

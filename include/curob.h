@@ -102,8 +102,19 @@ curob_status curob_dispose(void);
 
 /* Sec. 1.3, func_evaluate(): out[n] = f_fid(x_n) in FP64 for n < N.  x, out:
  * device pointers (x: N*D doubles, out: N doubles).  0 <= N <= max_concurrency.
- * Errors: NOT_INITIALIZED, INVALID_FID, INVALID_DIM, CAPACITY, NULL_POINTER,
- * INVALID_ARGUMENT, CUDA.  Asynchronous on `stream`. */
+ * The path is set by curob_set_precision64: on the tensor cores (default
+ * where the device has them) the block rotation is an error-free split
+ * product of BF16 integer digits (z rounded once to FP64 from an exact
+ * integer sum of all products above 2^-56 of the scale), with scratch (about
+ * 230 bytes per candidate and K step of 16 variables of the rotated blocks,
+ * plus 8 bytes per candidate and variable of every component; at most 2 GB
+ * per slice of candidates) taken stream-ordered from the library's pool;
+ * terms, sums and the composition are evaluated in FP64 as on the CUDA
+ * cores.  Calls with N at most the small-population limit (see
+ * curob_set_small_batch) run on the small kernels.  Errors: NOT_INITIALIZED,
+ * INVALID_FID, INVALID_DIM, CAPACITY, NULL_POINTER, INVALID_ARGUMENT,
+ * UNSUPPORTED (tensor cores forced where the device has none), CUDA.
+ * Asynchronous on `stream`. */
 curob_status curob_evaluate(int fid, const double* x, int N, double* out, curob_stream_t stream);
 
 /* Sec. 1.3, func_evaluatef(): the same with FP32 x and out.  The shift x - o
@@ -138,6 +149,32 @@ curob_status curob_h_evaluatef(int fid, const float* x, int N, float* out);
 /* Select the precision of curob_evaluatef (see curob_precision; every value
  * but MIXED; INVALID_ARGUMENT otherwise). */
 curob_status curob_set_precision(int mode);
+
+/* Paths of curob_evaluate (FP64) for calls beyond the small-population
+ * kernels. */
+typedef enum {
+  CUROB_PRECISION64_AUTO = 0,   /* TENSOR where the device runs tcgen05, else SIMT */
+  CUROB_PRECISION64_SIMT = 1,   /* FP64 pipe: each dot product one fma per term in index order */
+  CUROB_PRECISION64_TENSOR = 2  /* seven BF16 digits per operand, 28 products on the tensor
+                                   cores, classes summed exactly, z rounded once */
+} curob_precision64;
+
+/* Select the path of curob_evaluate (a curob_precision64 value;
+ * INVALID_ARGUMENT otherwise).  curob_initialize restores AUTO. */
+curob_status curob_set_precision64(int mode);
+
+/* The path curob_evaluate takes for fid beyond the small kernels
+ * (CUROB_PRECISION64_TENSOR or _SIMT, AUTO resolved).  Errors:
+ * NOT_INITIALIZED, INVALID_FID, INVALID_DIM, NULL_POINTER, UNSUPPORTED
+ * (TENSOR forced where the device has no tcgen05). */
+curob_status curob_query_precision64(int fid, int* mode);
+
+/* Kernel launches curob_evaluate(fid, ., N, ., .) makes: 1 on the small and
+ * SIMT kernels; on the tensor cores, per slice of candidates, the digit
+ * launch, a tensor-core launch when the function has a rotated block, and the
+ * finish launch.  Errors: as curob_query_precision64, and INVALID_ARGUMENT
+ * for N < 0. */
+curob_status curob_query_launches64(int fid, int N, int* launches);
 
 /* Small populations (the paper's timing setting, Sec. 2: 50 candidates per
  * call).  A call with N <= max_n candidates -- curob_evaluate, and

@@ -23,6 +23,9 @@ CODES = {v: k for k, v in STATUS.items()}
 PRECISION_AUTO, PRECISION_TF32X3, PRECISION_BF16X3, PRECISION_SIMT, PRECISION_EXACT = 0, 1, 2, 3, 4
 PRECISION_MIXED = 5  # reported for compositions whose members take different precisions
 PRECISION_FP16X3 = 6
+PRECISION64_AUTO = 0
+PRECISION64_SIMT = 1
+PRECISION64_TENSOR = 2
 NUM_FUNCTIONS = 37
 FOPT = 100.0
 
@@ -44,6 +47,9 @@ _SIGS = [
     ("curob_query_precision", _I, [_I, _P]),
     ("curob_query_component_precision", _I, [_I, _I, _P]),
     ("curob_query_launches", _I, [_I, _I, _P]),
+    ("curob_set_precision64", _I, [_I]),
+    ("curob_query_precision64", _I, [_I, _P]),
+    ("curob_query_launches64", _I, [_I, _I, _P]),
     ("curob_get_device_status", _I, [_P]),
     ("curob_selftest_bounded_wait", _I, [_P]),
     ("curob_status_string", ctypes.c_char_p, [_I]),
@@ -199,6 +205,22 @@ def curob_query_component_precision(fid, comp):
 def curob_query_launches(fid, N):
     n = ctypes.c_int()
     _call("curob_query_launches", fid, N, ctypes.addressof(n))
+    return n.value
+
+
+def curob_set_precision64(mode, check=True):
+    return _call("curob_set_precision64", mode, check=check)
+
+
+def curob_query_precision64(fid):
+    m = ctypes.c_int()
+    _call("curob_query_precision64", fid, ctypes.addressof(m))
+    return m.value
+
+
+def curob_query_launches64(fid, N):
+    n = ctypes.c_int()
+    _call("curob_query_launches64", fid, N, ctypes.addressof(n))
     return n.value
 
 

@@ -22,10 +22,11 @@ EXTRA = {
     "curob_simt64.cu": ["-fmad=false"],
     "curob_setup.cu": ["-fmad=false"],
     "curob_small64.cu": ["-fmad=false"],
+    "curob_f64tc.cu": ["-fmad=false"],
 }
 SOURCES = ["curob_api.cu", "curob_instance.cu", "curob_setup.cu", "curob_simt64.cu",
            "curob_simt32.cu", "curob_small64.cu", "curob_small32.cu", "curob_mma.cu",
-           "curob_batch.cu", "curob_mlp.cu"]
+           "curob_batch.cu", "curob_mlp.cu", "curob_f64tc.cu"]
 
 
 def _deps():

@@ -27,6 +27,7 @@ struct State {
   int max_conc = 0;
   int device = 0;
   int precision = CUROB_PRECISION_AUTO;
+  int precision64 = CUROB_PRECISION64_AUTO;
   int small_batch = kSmallBatchDefault;  // calls with N <= this take the small kernels
   Instance inst;
   void* d_hx = nullptr;   // host-wrapper staging (max_conc x D doubles)
@@ -116,6 +117,34 @@ int resolve_precision(const Function& F) {
   if (mode == CUROB_PRECISION_AUTO)
     mode = mma_ok ? mma_auto_mode(g.inst.mma, F) : CUROB_PRECISION_SIMT;
   return mode;
+}
+
+// The path curob_evaluate takes for fid at N candidates beyond the small
+// kernels: CUROB_PRECISION64_TENSOR or _SIMT, or -1 when the tensor cores are
+// forced but unavailable.
+int resolve_precision64(int fid) {
+  const bool tc = f64_supports(g.inst.f64, fid);
+  if (g.precision64 == CUROB_PRECISION64_TENSOR) return tc ? CUROB_PRECISION64_TENSOR : -1;
+  if (g.precision64 == CUROB_PRECISION64_SIMT) return CUROB_PRECISION64_SIMT;
+  return tc ? CUROB_PRECISION64_TENSOR : CUROB_PRECISION64_SIMT;
+}
+
+bool use_small(const Function& F, int N);
+
+// curob_evaluate's kernels for one batch already on the device.
+curob_status eval64(int fid, const double* x, int n, double* out, cudaStream_t st) {
+  const Function& F = g.inst.func[fid];
+  cudaError_t e;
+  if (use_small(F, n)) {
+    e = launch_small_f64(g.small[fid], x, n, out, st);
+  } else {
+    const int path = resolve_precision64(fid);
+    if (path < 0) return CUROB_ERR_UNSUPPORTED;
+    e = path == CUROB_PRECISION64_TENSOR
+            ? launch_f64tc(g.inst.f64, g.inst.mma.pool, tables(), F, fid, x, n, out, st)
+            : launch_simt_f64(tables(), F, x, n, out, st);
+  }
+  return e == cudaSuccess ? CUROB_OK : CUROB_ERR_CUDA;
 }
 
 // The small kernels' by-value copy of a function's segments and components.
@@ -212,6 +241,7 @@ curob_status curob_initialize(int D, int max_concurrency, uint64_t seed) {
     return rc;
   }
   g.precision = CUROB_PRECISION_AUTO;
+  g.precision64 = CUROB_PRECISION64_AUTO;
   g.small_batch = kSmallBatchDefault;
   for (int fid = 0; fid < kNumFunctions; ++fid)
     if (g.inst.func_ok[fid]) make_small_args(g.small[fid], g.inst.func[fid]);
@@ -232,11 +262,7 @@ curob_status curob_evaluate(int fid, const double* x, int N, double* out, curob_
   if (rc != CUROB_OK || N == 0) return rc;
   if (!on_instance_device()) return CUROB_ERR_INVALID_ARGUMENT;
   if (!device_accessible(x) || !device_accessible(out)) return CUROB_ERR_INVALID_ARGUMENT;
-  const Function& F = g.inst.func[fid];
-  cudaError_t e = use_small(F, N)
-                      ? launch_small_f64(g.small[fid], x, N, out, (cudaStream_t)stream)
-                      : launch_simt_f64(tables(), F, x, N, out, (cudaStream_t)stream);
-  return e == cudaSuccess ? CUROB_OK : CUROB_ERR_CUDA;
+  return eval64(fid, x, N, out, (cudaStream_t)stream);
 }
 
 curob_status curob_evaluatef(int fid, const float* x, int N, float* out, curob_stream_t stream) {
@@ -265,12 +291,9 @@ curob_status curob_h_evaluate(int fid, const double* x, int N, double* out) {
   // the staging buffers and the streams are shared: one host call at a time
   std::lock_guard<std::mutex> lk(g.mu);
   if (!on_instance_device()) return CUROB_ERR_INVALID_ARGUMENT;
-  const Function& F = g.inst.func[fid];
   return host_pipeline<double>(x, N, out, [&](const double* dx, int n, double* dout,
                                               cudaStream_t st) {
-    const cudaError_t e = use_small(F, n) ? launch_small_f64(g.small[fid], dx, n, dout, st)
-                                          : launch_simt_f64(tables(), F, dx, n, dout, st);
-    return e == cudaSuccess ? CUROB_OK : CUROB_ERR_CUDA;
+    return eval64(fid, dx, n, dout, st);
   });
 }
 
@@ -342,6 +365,37 @@ curob_status curob_query_launches(int fid, int N, int* launches) {
   else if (m == CUROB_PRECISION_SIMT) *launches = 1;
   else if (g.precision == CUROB_PRECISION_AUTO && use_small(g.inst.func[fid], N)) *launches = 1;
   else *launches = mma_launch_count(g.inst.func[fid], m, N);
+  return CUROB_OK;
+}
+
+curob_status curob_set_precision64(int mode) {
+  if (mode < CUROB_PRECISION64_AUTO || mode > CUROB_PRECISION64_TENSOR)
+    return CUROB_ERR_INVALID_ARGUMENT;
+  g.precision64 = mode;
+  return CUROB_OK;
+}
+
+curob_status curob_query_precision64(int fid, int* mode) {
+  if (!g.init) return CUROB_ERR_NOT_INITIALIZED;
+  if (fid < 0 || fid >= kNumFunctions) return CUROB_ERR_INVALID_FID;
+  if (!g.inst.func_ok[fid]) return CUROB_ERR_INVALID_DIM;
+  if (!mode) return CUROB_ERR_NULL_POINTER;
+  const int path = resolve_precision64(fid);
+  if (path < 0) return CUROB_ERR_UNSUPPORTED;
+  *mode = path;
+  return CUROB_OK;
+}
+
+curob_status curob_query_launches64(int fid, int N, int* launches) {
+  int m = 0;
+  curob_status rc = curob_query_precision64(fid, &m);
+  if (rc != CUROB_OK) return rc;
+  if (!launches) return CUROB_ERR_NULL_POINTER;
+  if (N < 0) return CUROB_ERR_INVALID_ARGUMENT;
+  const Function& F = g.inst.func[fid];
+  if (N == 0) *launches = 0;
+  else if (use_small(F, N) || m == CUROB_PRECISION64_SIMT) *launches = 1;
+  else *launches = f64_launch_count(g.inst.f64, F, fid, g.inst.D, N);
   return CUROB_OK;
 }
 

@@ -266,7 +266,10 @@ curob_status Instance::generate_all() {
   for (const Segment& s : segs)
     if (s.aux_off >= 0) aj.push_back(AuxJob{s.aux_off, s.kind, s.n, s.gn, s.gpos});
 
-  if (2 * (size_t)max_n * sizeof(double) > 220 * 1024) return CUROB_ERR_UNSUPPORTED;
+  if (8 * (size_t)max_n * sizeof(double) > 220 * 1024) return CUROB_ERR_UNSUPPORTED;
+  // the longest Gram-Schmidt chains first (each block is done by one warp)
+  std::stable_sort(gj.begin(), gj.end(),
+                   [](const GaussJob& a, const GaussJob& b) { return a.n > b.n; });
 
   PermJob* d_pj = nullptr;
   GaussJob* d_gj = nullptr;
@@ -338,6 +341,7 @@ void Instance::release() {
   d_Rt = nullptr; d_R32t = d_R32lot = nullptr;
   cudaFree(d_aux32); cudaFree(d_status);
   mma_release(mma);
+  f64_release(f64);
   d_seg = nullptr; d_comp = nullptr; d_o = d_operm = d_R = d_aux = nullptr;
   d_S = nullptr; d_R32 = d_R32lo = d_aux32 = nullptr; d_status = nullptr;
   segs.clear(); comps.clear(); chost.clear();
@@ -378,6 +382,7 @@ curob_status Instance::create(int D_, uint64_t seed_) {
   }
   curob_status rc = generate_all();
   if (rc == CUROB_OK) rc = mma_prepare(mma, segs, tables(), nullptr);
+  if (rc == CUROB_OK) rc = f64_prepare(f64, segs, comps, func, func_ok, tables());
   if (rc == CUROB_OK &&
       (cudaMemcpy(d_seg, segs.data(), sizeof(Segment) * segs.size(), cudaMemcpyHostToDevice) !=
            cudaSuccess ||
@@ -459,7 +464,8 @@ curob_status Instance::set_component(int fid, int comp, const double* o, const i
   cudaFree(d_pj);
   if (e != cudaSuccess) return CUROB_ERR_CUDA;
   std::vector<int> ids = ch.segs;
-  return mma_refresh(mma, segs, ids, tables());
+  const curob_status rc = mma_refresh(mma, segs, ids, tables());
+  return rc == CUROB_OK ? f64_refresh(f64, segs, ids, tables()) : rc;
 }
 
 }  // namespace curob

@@ -7,6 +7,7 @@
 
 #include "../../include/curob.h"
 #include "curob_internal.hpp"
+#include "curob_f64tc.hpp"
 #include "curob_mma.hpp"
 
 namespace curob {
@@ -39,6 +40,7 @@ class Instance {
   int* d_status = nullptr;
   long long r_total = 0, aux_total = 0;
   MmaPlan mma;  // tensor-core operand images
+  F64Plan f64;  // digit images of the tensor-core FP64 evaluator
 
   // Builds every function's instance for (D, seed) on the current device.
   curob_status create(int D, uint64_t seed);

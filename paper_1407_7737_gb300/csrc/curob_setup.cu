@@ -82,16 +82,22 @@ __global__ void gauss_kernel(const GaussJob* jobs, uint64_t seed, double* R) {
 // contraction), so the rows are the same function of the Gaussian entries
 // whatever the launch shape.  One warp per block: the lanes form the products
 // and apply the updates, lane 0 adds the products in order.  Sequential by
-// nature (O(n^3) dependent additions per block); setup only.
-__global__ void __launch_bounds__(32) gram_schmidt_kernel(const GaussJob* jobs, double* Rall,
-                                                          int* status) {
-  extern __shared__ double sm[];
-  const GaussJob J = jobs[blockIdx.x];
+// nature (O(n^3) dependent additions per block); setup only.  A CTA holds
+// four warps, each with a block of its own, so that every warp has an FP64
+// pipe to itself (one per scheduler); the largest blocks come first.
+constexpr int kGsWarps = 4;
+__global__ void __launch_bounds__(32 * kGsWarps) gram_schmidt_kernel(const GaussJob* jobs,
+                                                                     int njobs, int max_n,
+                                                                     double* Rall, int* status) {
+  extern __shared__ double smem_gs[];
+  const int job = blockIdx.x * kGsWarps + (threadIdx.x >> 5);
+  if (job >= njobs) return;  // uniform over the warp; the kernel has no CTA barrier
+  const GaussJob J = jobs[job];
   const int n = J.n;
   double* R = Rall + J.r_off;
-  double* v = sm;      // the row being orthonormalised
-  double* p = sm + n;  // products of the current dot product
-  const int lane = threadIdx.x;
+  double* v = smem_gs + (size_t)(threadIdx.x >> 5) * 2 * max_n;  // the row being orthonormalised
+  double* p = v + n;                                             // products of a dot product
+  const int lane = threadIdx.x & 31;
   // sum_c p[c] in index order, starting from 0 (lane 0), sent to every lane
   auto ordered_sum = [&]() -> double {
     __syncwarp();
@@ -204,13 +210,14 @@ cudaError_t launch_gauss_gs(const GaussJob* d_jobs, int njobs, int max_n, uint64
                             int* status, cudaStream_t st) {
   if (njobs == 0) return cudaSuccess;
   gauss_kernel<<<njobs, 256, 0, st>>>(d_jobs, seed, R);
-  size_t smem = 2 * (size_t)max_n * sizeof(double);
+  size_t smem = kGsWarps * 2 * (size_t)max_n * sizeof(double);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(gram_schmidt_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  gram_schmidt_kernel<<<njobs, 32, smem, st>>>(d_jobs, R, status);
+  gram_schmidt_kernel<<<(njobs + kGsWarps - 1) / kGsWarps, 32 * kGsWarps, smem, st>>>(
+      d_jobs, njobs, max_n, R, status);
   return cudaGetLastError();
 }
 

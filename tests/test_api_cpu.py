@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def declared_symbols():
     src = open(os.path.join(ROOT, "include", "curob.h")).read()
-    return sorted(set(re.findall(r"\b(curob_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(curob_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
