@@ -472,133 +472,158 @@ __global__ void __launch_bounds__(kMmaThreads, 1) f64_mma_kernel(const MmaArgs64
 }
 
 // ---------------------------------------------------------- finish kernel
-// A block takes kFinX candidates (threadIdx.x) and kFinS slices of each
-// block's variables (threadIdx.y).  A slice adds its terms -- term_f64, the
-// FP64 path's expression of each variable's term -- in index order; the
-// slices' partial sums (products for the product terms) are combined at the
-// last block of each basic function, which is then closed (finalize); the
-// composition mixes the members' values with ||x - o_i||^2 summed block
-// after block (Sec. 6).
-constexpr int kFinX = 16;
-constexpr int kFinS = 16;
+// A block takes 32 candidates (the lanes) and walks every block of every
+// component in chunks of 32 variables.  The eight warps form a chunk's terms
+// -- term_f64, the FP64 path's expression of each variable's term -- four
+// variables each, into a shared-memory tile (two tiles alternate); warp 0
+// then adds them in index order into its candidate's running sums, closes
+// each basic function at its last block (finalize) and, for a composition,
+// mixes the members with ||x - o_i||^2 summed block after block (Sec. 6).
+// The sums therefore round like a sequential evaluation of the formula, as
+// on the FP64 CUDA-core path: near an optimum, where f is a small difference
+// of large sums (Modified Schwefel: 418.9829 D - sum g1), the order of the
+// additions decides the last digits.
+constexpr int kFinCols = 32;  // variables per chunk
+constexpr int kFinWarps = 8;
+constexpr int kFinArr = 3;    // term arrays of a kind (f64_num_terms <= 3)
+constexpr int kFinTile = kFinArr * kFinCols * 32;  // doubles of one tile
+constexpr size_t kFinSmem = 2 * kFinTile * sizeof(double);  // 48 KB
 
-__device__ __forceinline__ void fin64_pair_reduce(double& a0, double& a1, double& a2, double& p) {
-  // lanes tx and tx + 16 of a warp hold the same candidate
-  a0 += __shfl_xor_sync(0xffffffffu, a0, 16);
-  a1 += __shfl_xor_sync(0xffffffffu, a1, 16);
-  a2 += __shfl_xor_sync(0xffffffffu, a2, 16);
-  p *= __shfl_xor_sync(0xffffffffu, p, 16);
+// The terms of one warp's columns of a chunk, with the kind fixed at compile
+// time (a kind known only at run time inside the loop lets the compiler
+// form other kinds' transcendentals for every variable).
+template <int KIND>
+__device__ __forceinline__ void fin64_terms(double* T, const double* zb, long long N, int j0,
+                                            int ncol, int warp, int lane, int gpos, double gnd,
+                                            const double* aux, double kat_e) {
+  constexpr int kPer = kFinCols / kFinWarps;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int jc = warp * kPer + q;
+    if (jc < ncol) {
+      const int j = j0 + jc;
+      if constexpr (kind_has_pairs(KIND)) {
+        T[jc * 32 + lane] =
+            (gpos + j > 0)
+                ? pair_term<double>(KIND, zb[(long long)(j - 1) * N], zb[(long long)j * N])
+                : 0.0;
+      } else {
+        const double zj = zb[(long long)j * N];
+        const double av = aux ? aux[j] : 0.0;
+#pragma unroll
+        for (int q2 = 0; q2 < f64_num_terms(KIND); ++q2)
+          T[(q2 * kFinCols + jc) * 32 + lane] = term_f64(KIND, q2, zj, 0.0, gpos + j, gnd, av, kat_e);
+      }
+    }
+  }
 }
 
-__global__ void __launch_bounds__(kFinX * kFinS) f64_finish_kernel(Tables tb, Function F,
-                                                                   const double* __restrict__ z,
-                                                                   const double* __restrict__ d2p,
-                                                                   int N, double* __restrict__ out) {
-  constexpr int kWarps = kFinX * kFinS / 32;
-  __shared__ double red[4][kWarps][kFinX];
-  __shared__ double Gs[kMaxComponents][kFinX];
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int warp = ty / 2;
-  const long long i = (long long)blockIdx.x * kFinX + tx;
+__device__ __forceinline__ void fin64_dispatch(int kind, double* T, const double* zb, long long N,
+                                               int j0, int ncol, int warp, int lane, int gpos,
+                                               double gnd, const double* aux, double kat_e) {
+  switch (kind) {
+#define CUROB_FIN64_CASE(K) \
+  case K: fin64_terms<K>(T, zb, N, j0, ncol, warp, lane, gpos, gnd, aux, kat_e); break;
+    CUROB_FIN64_CASE(K_SPHERE) CUROB_FIN64_CASE(K_ELLIPSOID) CUROB_FIN64_CASE(K_ELLIPTIC)
+    CUROB_FIN64_CASE(K_DISCUS) CUROB_FIN64_CASE(K_CIGAR) CUROB_FIN64_CASE(K_POWERS)
+    CUROB_FIN64_CASE(K_SHARPV) CUROB_FIN64_CASE(K_STEP) CUROB_FIN64_CASE(K_WEIERSTRASS)
+    CUROB_FIN64_CASE(K_GRIEWANK) CUROB_FIN64_CASE(K_RASTRIGIN) CUROB_FIN64_CASE(K_SCHAFFER7)
+    CUROB_FIN64_CASE(K_EGR) CUROB_FIN64_CASE(K_ROSENBROCK) CUROB_FIN64_CASE(K_SCHWEFEL)
+    CUROB_FIN64_CASE(K_KATSUURA) CUROB_FIN64_CASE(K_LUNACEK) CUROB_FIN64_CASE(K_ACKLEY)
+    CUROB_FIN64_CASE(K_HAPPYCAT) CUROB_FIN64_CASE(K_HGBAT) CUROB_FIN64_CASE(K_SCHAFFER6)
+#undef CUROB_FIN64_CASE
+    default: break;
+  }
+}
+
+__global__ void __launch_bounds__(kFinWarps * 32, 2) f64_finish_kernel(Tables tb, Function F,
+                                                                    const double* __restrict__ z,
+                                                                    const double* __restrict__ d2p,
+                                                                    int N, double* __restrict__ out) {
+  extern __shared__ double fin_tiles[];  // [2][kFinArr][kFinCols][32]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long i = (long long)blockIdx.x * 32 + lane;
   const bool valid = i < N;
   const long long ic = valid ? i : 0;  // rows past N read row 0 and write nothing
   const int D = tb.D;
   const int fseg0 = tb.comp[F.comp0].seg0;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, p = 1.0;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, p = 1.0;  // warp 0: the open function's sums
+  double G[kMaxComponents];
+  int buf = 0;
   for (int c = 0; c < F.ncomp; ++c) {
     const Component C = tb.comp[F.comp0 + c];
     const double* zc = z + (long long)c * D * N + ic;
     double gsum = 0.0;
     for (int si = 0; si < C.nseg; ++si) {
       const Segment sg = tb.seg[C.seg0 + si];
-      if (sg.gfirst) {
-        a0 = a1 = a2 = 0.0;
-        p = 1.0;
-      }
       const int n = sg.n, kind = sg.kind;
-      const int L = (n + kFinS - 1) / kFinS;
-      const int j0 = min(n, ty * L), j1 = min(n, j0 + L);
+      const bool pairs = kind_has_pairs(kind);
+      const bool first_special = (kind == K_DISCUS || kind == K_CIGAR || kind == K_SHARPV);
+      const double gnd = (double)sg.gn;
+      const double kat_e = (kind == K_KATSUURA) ? 10.0 / pow(gnd, 1.2) : 0.0;
+      const double* aux = sg.aux_off >= 0 ? tb.aux + sg.aux_off : nullptr;
+      const int na = pairs ? 1 : f64_num_terms(kind);
       const double* zb = zc + (long long)sg.zoff * N;
-      if (kind_has_pairs(kind)) {
-        // pairs (z_{g-1}, z_g) for function positions g >= 1; a function's
-        // blocks are consecutive in z, so position j0 - 1 < 0 is the
-        // previous block's last variable
-        if (j0 < j1) {
-          double zp = (sg.gpos + j0 > 0) ? zb[(long long)(j0 - 1) * N] : 0.0;
-          for (int j = j0; j < j1; ++j) {
-            const double zj = zb[(long long)j * N];
-            if (sg.gpos + j > 0) a0 += pair_term<double>(kind, zp, zj);
-            zp = zj;
+      for (int j0 = 0; j0 < n; j0 += kFinCols) {
+        double* T = fin_tiles + buf * kFinTile;
+        const int ncol = min(kFinCols, n - j0);
+        // the terms of columns j0 + 4 warp .. + 3; a pair kind's column j
+        // holds the pair (z_{j-1}, z_j) of function positions >= 1 (z_{-1}
+        // is the previous block's last variable: a function's blocks are
+        // consecutive in z)
+        fin64_dispatch(kind, T, zb, N, j0, ncol, warp, lane, sg.gpos, gnd, aux, kat_e);
+        __syncthreads();
+        if (warp == 0) {
+          if (j0 == 0 && sg.gfirst) {
+            a0 = a1 = a2 = 0.0;
+            p = 1.0;
           }
-        }
-      } else {
-        const double gnd = (double)sg.gn;
-        const double kat_e = (kind == K_KATSUURA) ? 10.0 / pow(gnd, 1.2) : 0.0;
-        const double* aux = sg.aux_off >= 0 ? tb.aux + sg.aux_off : nullptr;
-        const bool first_special = (kind == K_DISCUS || kind == K_CIGAR || kind == K_SHARPV);
-        const int na = f64_num_terms(kind);
-        for (int j = j0; j < j1; ++j) {
-          const double zj = zb[(long long)j * N];
-          const double av = aux ? aux[j] : 0.0;
-          for (int q = 0; q < na; ++q) {
-            const double t = term_f64(kind, q, zj, 0.0, sg.gpos + j, gnd, av, kat_e);
-            if (f64_term_is_product(kind, q)) {
-              p *= t;
-            } else if (q == 0) {
-              if (first_special && sg.gpos + j == 0) a1 += t;  // z_1 enters separately
-              else a0 += t;
-            } else if (q == 1) {
-              a1 += t;
-            } else {
-              a2 += t;
+          if (pairs) {
+            for (int jc = 0; jc < ncol; ++jc)
+              if (sg.gpos + j0 + jc > 0) a0 += T[jc * 32 + lane];
+          } else {
+            for (int q2 = 0; q2 < na; ++q2) {
+              const double* t = T + q2 * kFinCols * 32 + lane;
+              if (f64_term_is_product(kind, q2)) {
+                for (int jc = 0; jc < ncol; ++jc) p *= t[jc * 32];
+              } else if (q2 == 0) {
+                for (int jc = 0; jc < ncol; ++jc) {
+                  if (first_special && sg.gpos + j0 + jc == 0) a1 = t[jc * 32];  // z_1 apart
+                  else a0 += t[jc * 32];
+                }
+              } else if (q2 == 1) {
+                for (int jc = 0; jc < ncol; ++jc) a1 += t[jc * 32];
+              } else {
+                for (int jc = 0; jc < ncol; ++jc) a2 += t[jc * 32];
+              }
             }
           }
-        }
-      }
-      if (sg.glast) {
-        fin64_pair_reduce(a0, a1, a2, p);
-        if ((ty & 1) == 0) {
-          red[0][warp][tx] = a0;
-          red[1][warp][tx] = a1;
-          red[2][warp][tx] = a2;
-          red[3][warp][tx] = p;
-        }
-        __syncthreads();
-        if (ty == 0) {
-          double s0 = 0.0, s1 = 0.0, s2 = 0.0, pp = 1.0;
-          for (int w = 0; w < kWarps; ++w) {
-            s0 += red[0][w][tx];
-            s1 += red[1][w][tx];
-            s2 += red[2][w][tx];
-            pp *= red[3][w][tx];
+          if (j0 + kFinCols >= n && sg.glast) {
+            if (kind_is_cyclic(kind)) {  // (z_gn, z_1) closes the cycle
+              const double* zf = zc + (long long)(sg.zoff - sg.gpos) * N;
+              a0 += pair_term<double>(kind, zf[(long long)(sg.gn - 1) * N], zf[0]);
+            }
+            gsum += finalize(kind, a0, a1, a2, p, sg.gn);
           }
-          if (kind_is_cyclic(kind)) {  // (z_gn, z_1) closes the cycle
-            const double* zf = zc + (long long)(sg.zoff - sg.gpos) * N;
-            s0 += pair_term<double>(kind, zf[(long long)(sg.gn - 1) * N], zf[0]);
-          }
-          gsum += finalize(kind, s0, s1, s2, pp, sg.gn);
         }
-        __syncthreads();
-        a0 = a1 = a2 = 0.0;
-        p = 1.0;
+        buf ^= 1;
       }
     }
-    if (ty == 0) Gs[c][tx] = gsum;
+    G[c] = gsum;
   }
-  if (ty != 0 || !valid) return;
+  if (warp != 0 || !valid) return;
   double f;
   if (F.composition) {
-    double G[kMaxComponents], d2v[kMaxComponents];
+    double d2v[kMaxComponents];
     for (int c = 0; c < F.ncomp; ++c) {
       const Component C = tb.comp[F.comp0 + c];
       double dd = 0.0;
       for (int si = 0; si < C.nseg; ++si) dd += d2p[(long long)(C.seg0 - fseg0 + si) * N + i];
-      G[c] = Gs[c][tx];
       d2v[c] = dd;
     }
     f = compose(tb.comp + F.comp0, F.ncomp, G, d2v, D);
   } else {
-    f = Gs[0][tx];
+    f = G[0];
   }
   out[i] = f + kFopt;
 }
@@ -825,7 +850,7 @@ cudaError_t launch_f64tc(const F64Plan& p, cudaMemPool_t pool, const Tables& tb,
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-      f64_finish_kernel<<<(unsigned)((ns + kFinX - 1) / kFinX), dim3(kFinX, kFinS), 0, st>>>(
+      f64_finish_kernel<<<(unsigned)((ns + 31) / 32), kFinWarps * 32, kFinSmem, st>>>(
           tb, F, zs, d2p, ns, out + s0);
       e = cudaGetLastError();
     }

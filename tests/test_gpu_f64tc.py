@@ -176,26 +176,37 @@ def test_f64tc_slices_and_launches(orc):
         _restore(cu)
 
 
+PHASE_KINDS = (8, 15)  # Weierstrass (3^k z phases), Katsuura (2^j z phases)
+
+
 def test_f64tc_scales_and_optimum(orc):
-    """Candidates far outside the box, at 1e-9 from o, and at o itself (y = 0:
-    every digit zero)."""
+    """Candidates ten times outside the box (|x| <= 1e3), at 1e-9 from o, and
+    at o itself (y = 0: every digit zero).  Outside the box, functions with a
+    Weierstrass or Katsuura member are left out of the comparison: the 3^20 z
+    (2^32 z) phases turn one ulp of z into a different f there, so no two
+    evaluations that do not share z's rounding agree (the FP64 CUDA-core
+    path agrees with the oracle only because it repeats its fma order); far
+    larger |x| does the same to every cosine term (2 pi |z| ulps of phase)."""
     D, N = 100, 512
     cu = gu.ensure(D, N)
     _tensor(cu)
     try:
         for fid in ALL:
+            kinds = {k for c in range(cu.curob_num_components(fid))
+                     for k in cu.curob_component_kinds(fid, c)}
+            lo = 128 if kinds & set(PHASE_KINDS) else 0
             comps = orc.generate(fid, D, 0)
             o = comps[0].o
             rng = np.random.default_rng(fid)
             x = np.empty((N, D))
-            x[:128] = rng.uniform(-1e6, 1e6, (128, D))
+            x[:128] = rng.uniform(-1e3, 1e3, (128, D))
             x[128:256] = o[None, :] + rng.normal(0, 1e-9, (128, D))
             x[256:384] = inputs.uniform(128, D, 60 + fid)
             x[384:] = o[None, :]
             ref = orc.evaluate(fid, D, 0, x, nthreads=16)
             got = gu.gpu_eval(fid, x, _torch().float64)
-            err = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)
-            assert err.max() <= TOL, (fid, float(err.max()), int(np.argmax(err)))
+            err = (np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300))[lo:]
+            assert err.max() <= TOL, (fid, float(err.max()), int(np.argmax(err)) + lo)
     finally:
         _restore(cu)
 
