@@ -802,8 +802,9 @@ def surrogate_bench(cu, torch, dev, stream, args, D_s=100, epochs=4, batch=4096,
 
 def ragged_batch(cu, torch, dev, stream, reps=5, n_items=64, seed=2024):
     """64 items, fid uniform over the suite, D uniform over {10, 30, 50, 100,
-    500, 1000}, N log-uniform in [32, 8192]: one persistent launch replayed
-    from a CUDA graph against one launch per item (same EXACT arithmetic)."""
+    500, 1000}, N log-uniform in [32, 8192]: the persistent launches (one per
+    precision) replayed from a CUDA graph, against every item as a
+    curob_evaluatef call under AUTO and against one fused launch per item."""
     from paper_1407_7737_gb300 import inputs
     items = inputs.ragged_instances(n_items, seed)
     xs, outs, spec = [], [], []
@@ -832,20 +833,31 @@ def ragged_batch(cu, torch, dev, stream, reps=5, n_items=64, seed=2024):
             return a.elapsed_time(z) / reps
 
         ms_p = timed(cu.curob_batch_run)
+        ms_a = timed(cu.curob_batch_run_auto)
         ms_s = timed(cu.curob_batch_run_separate)
         cu.curob_batch_status(b, stream)
         nwork, grid, order = cu.curob_batch_schedule(b)
+        plan = cu.curob_batch_plan(b)
     finally:
         cu.curob_batch_destroy(b)
+    names = ["longest-first", "round-robin", "item-order"]
     return {"items": n_items, "evals_per_run": evals,
             "dims": sorted({D for (_, D, _) in items}),
-            "persistent_graph_ms": round(ms_p, 4), "separate_launches_ms": round(ms_s, 4),
+            "persistent_graph_ms": round(ms_p, 4),
+            "per_item_auto_calls_ms": round(ms_a, 4),
+            "separate_fused_launches_ms": round(ms_s, 4),
             "persistent_evals_s": round(evals / (ms_p / 1e3), 1),
-            "separate_evals_s": round(evals / (ms_s / 1e3), 1),
-            "speedup": round(ms_s / ms_p, 3),
-            "schedule": {"work_items": nwork, "grid": grid,
-                         "order": ["longest-first", "round-robin", "item-order"][order]},
-            "precision": "exact (all items)"}
+            "per_item_auto_evals_s": round(evals / (ms_a / 1e3), 1),
+            "speedup_vs_per_item_auto": round(ms_a / ms_p, 3),
+            "speedup_vs_separate_fused": round(ms_s / ms_p, 3),
+            "schedule": {"work_items": nwork, "grid": grid, "order": names[order]},
+            "autotuner": {"items_exact": plan["items_exact"], "items_tf32x3": plan["items_tf32"],
+                          "work_exact": plan["work_exact"], "work_tf32x3": plan["work_tf32"],
+                          "grid_exact": plan["grid_exact"], "grid_tf32x3": plan["grid_tf32"],
+                          "order_exact": names[plan["order_exact"]],
+                          "order_tf32x3": names[plan["order_tf32"]],
+                          "launches": "side by side" if plan["concurrent"] else "in sequence"},
+            "precision": "per item, AUTO's rule (TF32X3 or EXACT)"}
 
 
 def cpu_baseline(sample_n=8, budget_s=25.0):

@@ -301,14 +301,18 @@ curob_status curob_evaluatef_multi_noalloc(const int* fids, const float* const* 
 /* ---------------------------------------------------------------------------
  * Ragged batches (this library's extension; the paper evaluates one function
  * at one D at a time).  A batch is a list of (function, D, seed, population)
- * items evaluated together by one persistent tensor-core kernel: each CTA of
- * a grid of at most one CTA per SM takes 128-candidate tiles of any item from
- * a work counter until none is left.  Every item uses the EXACT contraction
- * (curob_precision), so any function at any block width up to 512 meets the
- * FP32 tolerance.  The first curob_batch_run times a few schedules (work
- * order, grid size), keeps the fastest, and captures it in a CUDA graph that
- * later runs replay.  A batch owns its instances (one per distinct D, seed);
- * it is independent of curob_initialize.
+ * items evaluated together by persistent tensor-core kernels: each CTA of a
+ * grid of at most one CTA per SM takes 128-candidate tiles of any item from a
+ * work counter until none is left.  Each item runs at the precision
+ * curob_evaluatef's AUTO rule gives its function (TF32X3 where no kind
+ * magnifies contraction error, else EXACT; a MIXED composition, and a function
+ * AUTO leaves to the CUDA cores, on EXACT), so every item meets the FP32
+ * tolerance; the items of each precision form one persistent launch.  The
+ * first curob_batch_run times a few schedules (work order per launch, the two
+ * launches in sequence or side by side on a split of the SMs), keeps the
+ * fastest, and captures it in a CUDA graph that later runs replay.  A batch
+ * owns its instances (one per distinct D, seed); it is independent of
+ * curob_initialize.
  * ------------------------------------------------------------------------- */
 typedef struct {
   int fid;          /* Table 1 ID */
@@ -333,14 +337,31 @@ curob_status curob_batch_create(const curob_batch_item* items, int n_items, curo
  * must not be made during a stream capture); later calls launch the graph. */
 curob_status curob_batch_run(curob_batch batch, curob_stream_t stream);
 
-/* The same work as one launch of the tensor-core kernel per item, in item
- * order (the baseline the persistent launch is measured against). */
+/* The same tile arithmetic as one fused launch of the tensor-core kernel per
+ * item, in item order, each at its item's precision (values equal to
+ * curob_batch_run's bit for bit). */
 curob_status curob_batch_run_separate(curob_batch batch, curob_stream_t stream);
 
+/* Every item as curob_evaluatef under CUROB_PRECISION_AUTO would evaluate it
+ * (small-population kernels for N <= 512, else the tensor-core launches with a
+ * finish kernel for heavy kinds and MIXED compositions, or the CUDA-core
+ * kernel), one item after another on `stream`: the per-call baseline the
+ * persistent launches are measured against.  Scratch as curob_evaluatef. */
+curob_status curob_batch_run_auto(curob_batch batch, curob_stream_t stream);
+
 /* Schedule chosen by the autotuner (host pointers, any may be NULL): number
- * of work items, grid size, order (0 = longest first, 1 = round robin over
- * items, 2 = item order).  NOT_INITIALIZED before the first run. */
+ * of work items, grid size (the sum of the two launches' grids when they run
+ * side by side), order of the costlier launch (0 = longest first, 1 = round
+ * robin over items, 2 = item order).  NOT_INITIALIZED before the first run. */
 curob_status curob_batch_schedule(curob_batch batch, int* n_work, int* grid, int* order);
+
+/* The autotuner's choices per precision (host pointers, any may be NULL):
+ * items and work items on EXACT and on TF32X3, each launch's grid (0 when it
+ * has no work) and work order, and whether the two launches run side by side
+ * (1) or one after the other (0).  NOT_INITIALIZED before the first run. */
+curob_status curob_batch_plan(curob_batch batch, int* items_exact, int* items_tf32,
+                              int* work_exact, int* work_tf32, int* grid_exact, int* grid_tf32,
+                              int* order_exact, int* order_tf32, int* concurrent);
 
 /* Synchronises `stream` and reports (then clears) a device-side error of any
  * of the batch's instances. */

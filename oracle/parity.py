@@ -107,3 +107,60 @@ def fp32_check(fid, D, seed, x32, got, rows=None, fscale=None, ref=None):
         ok = ok | edge
     ratio = np.abs(got[r] - ref) / tol
     return bool(ok.all()), float(ratio[ok].max() if ok.any() else np.inf), excused, float(ratio.max())
+
+
+def _mirror(kind, zj):
+    """zj reflected across the nearest jump of its kind (same distance, other
+    side)."""
+    if kind == "step":
+        v = zj + 0.5
+        return 2.0 * np.round(v) - v - 0.5
+    c = 420.9687462275036
+    w = zj + c
+    a = abs(w)
+    jump = np.round(a / 500.0) * 500.0
+    return np.copysign(2.0 * jump - a, w) - c
+
+
+def explain_excused(fid, D, seed, x32, got, rows=None, fscale=None):
+    """For each row fp32_check excuses: the discontinuous variable nearest its
+    jump (member, index in the member's z, its z and distance to the jump),
+    the oracle's f at the FP32-rounded x (its FP64 z) and the oracle's f with
+    that one variable reflected to the other side of the jump, and whether the
+    GPU value matches the other side within the FP32 tolerance -- i.e. whether
+    the FP32 rounding of z crossed the jump."""
+    r = np.arange(x32.shape[0]) if rows is None else np.asarray(rows)
+    xr = np.asarray(x32[r], dtype=np.float64)
+    ref = oracle.evaluate(fid, D, seed, xr, nthreads=16)
+    fs = f_scale(fid, D, seed) if fscale is None else fscale
+    ok, tol = fp32_ok(got[r], ref, fs)
+    if fid not in DISC or ok.all():
+        return []
+    edge = near_discontinuity(fid, D, seed, xr)
+    comps = oracle.generate(fid, D, seed)
+    out = []
+    for i in np.nonzero(~ok & edge)[0]:
+        x = xr[i]
+        zs = [oracle.component_z(fid, D, comps, c, x) for c in range(len(comps))]
+        d2 = [float(np.sum((x - cc.o) ** 2)) for cc in comps]
+        best = None
+        for comp, block, kind, scale in DISC[fid]:
+            sizes = comps[comp].blocks
+            lo = 0 if block is None else int(sum(sizes[:block]))
+            hi = D if block is None else lo + int(sizes[block])
+            dist, v = jump_distance(kind, zs[comp][lo:hi])
+            rel = dist / (np.abs(v) + 1.0)
+            j = int(np.argmin(rel))
+            if best is None or rel[j] < best[0]:
+                best = (float(rel[j]), comp, lo + j, kind, float(dist[j]))
+        _, comp, j, kind, dist = best
+        zo = [z.copy() for z in zs]
+        zo[comp][j] = _mirror(kind, zs[comp][j])
+        f_other = oracle.evaluate_from_z(fid, D, zo, d2)
+        out.append({"row": int(r[i]), "gpu": float(got[r[i]]), "oracle": float(ref[i]),
+                    "oracle_other_side": f_other, "tol": float(tol[i]),
+                    "ratio": float(abs(got[r[i]] - ref[i]) / tol[i]),
+                    "member": comp, "z_index": j, "kind": kind, "z": float(zs[comp][j]),
+                    "distance_to_jump": dist,
+                    "gpu_on_other_side": bool(abs(got[r[i]] - f_other) <= tol[i])})
+    return out

@@ -63,6 +63,8 @@ _SIGS = [
     ("curob_batch_create", _I, [_P, _I, _P]),
     ("curob_batch_run", _I, [_P, _P]),
     ("curob_batch_run_separate", _I, [_P, _P]),
+    ("curob_batch_run_auto", _I, [_P, _P]),
+    ("curob_batch_plan", _I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     ("curob_batch_schedule", _I, [_P, _P, _P, _P]),
     ("curob_batch_status", _I, [_P, _P]),
     ("curob_batch_destroy", _I, [_P]),
@@ -325,6 +327,19 @@ def curob_batch_run(batch, stream=None, check=True):
 
 def curob_batch_run_separate(batch, stream=None, check=True):
     return _call("curob_batch_run_separate", batch, _stream(stream), check=check)
+
+
+def curob_batch_run_auto(batch, stream=None, check=True):
+    return _call("curob_batch_run_auto", batch, _stream(stream), check=check)
+
+
+def curob_batch_plan(batch):
+    """dict of the autotuner's choices per precision."""
+    v = [ctypes.c_int() for _ in range(9)]
+    _call("curob_batch_plan", batch, *[ctypes.addressof(a) for a in v])
+    keys = ("items_exact", "items_tf32", "work_exact", "work_tf32", "grid_exact", "grid_tf32",
+            "order_exact", "order_tf32", "concurrent")
+    return {k: a.value for k, a in zip(keys, v)}
 
 
 def curob_batch_schedule(batch):

@@ -148,14 +148,7 @@ curob_status eval64(int fid, const double* x, int n, double* out, cudaStream_t s
 }
 
 // The small kernels' by-value copy of a function's segments and components.
-void make_small_args(SmallArgs& a, const Function& F) {
-  memset(&a, 0, sizeof(a));
-  a.tb = g.inst.tables();
-  a.F = F;
-  a.seg_base = g.inst.comps[F.comp0].seg0;
-  for (int i = 0; i < F.nseg && i < kSmallMaxWarps; ++i) a.seg[i] = g.inst.segs[a.seg_base + i];
-  for (int c = 0; c < F.ncomp; ++c) a.comp[c] = g.inst.comps[F.comp0 + c];
-}
+void make_small_args(SmallArgs& a, const Function& F) { fill_small_args(a, g.inst, F); }
 
 // A call of N candidates takes the small-population kernels (FP64, and the
 // FP32 path under AUTO) when N is within the limit and every block fits them.

@@ -1,7 +1,16 @@
 // curob_batch.cu -- ragged batches (include/curob.h, curob_batch_*): many
-// (function, D, seed, population) items evaluated by one persistent
-// tensor-core launch, scheduled by a small autotuner and replayed from a
-// CUDA graph.
+// (function, D, seed, population) items evaluated by persistent tensor-core
+// launches, scheduled by a small autotuner and replayed from a CUDA graph.
+//
+// Each item takes the precision curob_evaluatef's AUTO rule gives its
+// function: TF32X3 where no kind magnifies contraction error, EXACT otherwise
+// (a composition whose members differ runs whole on EXACT, and so does a
+// function with blocks narrower than 16, which AUTO sends to the CUDA-core
+// kernel).  The items of each precision form one persistent launch.  The
+// tuner times three work orders per launch on a full grid, then whether the
+// two launches run one after the other or side by side on a split of the SMs
+// (the split from the estimated costs, and its two neighbours), keeps the
+// fastest and captures it in a CUDA graph.
 #include <algorithm>
 #include <map>
 #include <memory>
@@ -12,6 +21,7 @@
 #include "../../include/curob.h"
 #include "curob_instance.hpp"
 #include "curob_mma.hpp"
+#include "curob_small.cuh"
 
 namespace curob {
 bool device_accessible(const void* p);
@@ -19,22 +29,38 @@ bool device_accessible(const void* p);
 
 using namespace curob;
 
+namespace {
+constexpr int kGroups = 2;        // 0: EXACT items, 1: TF32X3 items
+constexpr int kSmallAuto = 512;   // AUTO's small-population limit (curob_set_small_batch default)
+
+struct Group {
+  int mode = CUROB_PRECISION_EXACT;
+  std::vector<int2> work_host[3];  // (item, tile) in each candidate order
+  int2* d_work[3] = {nullptr, nullptr, nullptr};
+  int nwork = 0;
+  int* d_counter = nullptr;
+  int npad_max = 32;               // widest block of the group's items, rounded up to 32
+  double cost = 0.0;               // estimated cost of the group's tiles
+  int order = 0, grid = 0;
+};
+}  // namespace
+
 struct curob_batch_st {
   std::vector<curob_batch_item> items;
   std::map<std::pair<int, uint64_t>, std::unique_ptr<Instance>> inst;
   std::vector<Instance*> item_inst;
+  std::vector<int> item_group;       // 0 EXACT, 1 TF32X3
   std::vector<double> tile_cost;     // estimated cost of one tile of each item
-  std::vector<int2> work_host[3];    // (item, tile) in each candidate order
-  int nwork = 0;
+  std::vector<SmallArgs> small;      // per item, for curob_batch_run_auto
+  Group grp[kGroups];
   void* d_args = nullptr;
-  int2* d_work[3] = {nullptr, nullptr, nullptr};
-  int* d_counter = nullptr;
   int nsm = 0;
   bool tuned = false;
-  int grid = 0, order = 0;
+  int concurrent = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaStream_t priv = nullptr;
+  cudaStream_t priv = nullptr, priv2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 namespace {
@@ -44,18 +70,19 @@ bool heavy_kind(int k) {
          k == K_EGR || k == K_SCHWEFEL || k == K_KATSUURA || k == K_SCHAFFER6;
 }
 
-// Cost of one 128-candidate tile: tensor work (npad^2 per block and N chunk
-// pass) plus the epilogue's per-variable work (heavier for transcendental
-// kinds).
-double tile_cost(const Instance& I, int fid) {
+// Cost of one 128-candidate tile: tensor work (npad^2 per block and
+// product: 10 on EXACT, 3 on TF32X3) plus the epilogue's per-variable work
+// (heavier for transcendental kinds).
+double tile_cost(const Instance& I, int fid, int group) {
   const Function& F = I.func[fid];
+  const double prod = group == 0 ? 10.0 : 3.0;
   double c = 0.0;
   for (int ci = 0; ci < F.ncomp; ++ci) {
     const Component& C = I.comps[F.comp0 + ci];
     for (int si = 0; si < C.nseg; ++si) {
       const Segment& s = I.segs[C.seg0 + si];
       const int npad = (s.n + 31) / 32 * 32;
-      c += (double)npad * npad * 10.0 / 64.0 + (double)s.n * (heavy_kind(s.kind) ? 40.0 : 4.0);
+      c += (double)npad * npad * prod / 64.0 + (double)s.n * (heavy_kind(s.kind) ? 40.0 : 4.0);
     }
   }
   return c;
@@ -66,24 +93,54 @@ void free_batch(curob_batch b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->priv) cudaStreamDestroy(b->priv);
+  if (b->priv2) cudaStreamDestroy(b->priv2);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
   cudaFree(b->d_args);
-  for (int o = 0; o < 3; ++o) cudaFree(b->d_work[o]);
-  cudaFree(b->d_counter);
+  for (Group& g : b->grp) {
+    for (int o = 0; o < 3; ++o) cudaFree(g.d_work[o]);
+    cudaFree(g.d_counter);
+  }
   for (auto& kv : b->inst) kv.second->release();
   delete b;
 }
 
-// Time one schedule (ms), two launches, the second measured.
-float time_schedule(curob_batch b, int order, int grid) {
+cudaError_t launch_group(curob_batch b, int gi, int order, int grid, cudaStream_t st) {
+  Group& g = b->grp[gi];
+  cudaError_t e = cudaMemsetAsync(g.d_counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  return launch_mma_batch(b->d_args, g.d_work[order], g.nwork, g.d_counter,
+                          std::min(grid, std::max(1, g.nwork)), st, g.mode, g.npad_max);
+}
+
+// Issues a schedule on b->priv: the groups in sequence, or side by side (the
+// TF32X3 group on priv2, forked from and joined back into priv).
+cudaError_t issue(curob_batch b, const int* order, const int* grid, bool concurrent) {
+  const bool both = b->grp[0].nwork > 0 && b->grp[1].nwork > 0;
+  cudaError_t e = cudaSuccess;
+  if (concurrent && both) {
+    e = cudaEventRecord(b->fork, b->priv);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->priv2, b->fork, 0);
+    if (e == cudaSuccess) e = launch_group(b, 0, order[0], grid[0], b->priv);
+    if (e == cudaSuccess) e = launch_group(b, 1, order[1], grid[1], b->priv2);
+    if (e == cudaSuccess) e = cudaEventRecord(b->join, b->priv2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->priv, b->join, 0);
+    return e;
+  }
+  for (int gi = 0; gi < kGroups && e == cudaSuccess; ++gi)
+    if (b->grp[gi].nwork > 0) e = launch_group(b, gi, order[gi], grid[gi], b->priv);
+  return e;
+}
+
+// Time one schedule (ms): two runs, the second measured.
+float time_schedule(curob_batch b, const int* order, const int* grid, bool concurrent) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float ms = -1.f;
   for (int rep = 0; rep < 2; ++rep) {
-    cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->priv);
     cudaEventRecord(e0, b->priv);
-    if (launch_mma_batch(b->d_args, b->d_work[order], b->nwork, b->d_counter, grid, b->priv) !=
-        cudaSuccess) {
+    if (issue(b, order, grid, concurrent) != cudaSuccess) {
       ms = -1.f;
       break;
     }
@@ -97,24 +154,56 @@ float time_schedule(curob_batch b, int order, int grid) {
 }
 
 curob_status tune_and_capture(curob_batch b) {
-  const int grids[2] = {b->nsm, std::max(1, b->nsm * 3 / 4)};
-  float best = 1e30f;
-  for (int order = 0; order < 3; ++order)
-    for (int gi = 0; gi < 2; ++gi) {
-      const int grid = std::min(grids[gi], std::max(1, b->nwork));
-      const float ms = time_schedule(b, order, grid);
+  int order[kGroups] = {0, 0}, grid[kGroups] = {b->nsm, b->nsm};
+  // the work order of each launch, alone on a full grid
+  for (int gi = 0; gi < kGroups; ++gi) {
+    if (b->grp[gi].nwork == 0) continue;
+    float best = 1e30f;
+    int sel[kGroups] = {0, 0};
+    for (int o = 0; o < 3; ++o) {
+      sel[gi] = o;
+      const int saved = b->grp[1 - gi].nwork;
+      b->grp[1 - gi].nwork = 0;  // time this launch alone
+      const float ms = time_schedule(b, sel, grid, false);
+      b->grp[1 - gi].nwork = saved;
       if (ms < 0.f) return CUROB_ERR_CUDA;
       if (ms < best) {
         best = ms;
-        b->order = order;
-        b->grid = grid;
+        order[gi] = o;
       }
     }
+  }
+  // one after the other on full grids, or side by side on a split
+  float best = time_schedule(b, order, grid, false);
+  if (best < 0.f) return CUROB_ERR_CUDA;
+  b->concurrent = 0;
+  b->grp[0].grid = grid[0];
+  b->grp[1].grid = grid[1];
+  if (b->grp[0].nwork > 0 && b->grp[1].nwork > 0 && b->nsm >= 4) {
+    const double share = b->grp[0].cost / std::max(1e-30, b->grp[0].cost + b->grp[1].cost);
+    const int g0 = (int)(share * b->nsm + 0.5);
+    const int step = std::max(1, b->nsm / 8);
+    for (int cand : {g0, g0 - step, g0 + step}) {
+      const int gE = std::min(b->nsm - 1, std::max(1, cand));
+      const int split[kGroups] = {gE, b->nsm - gE};
+      const float ms = time_schedule(b, order, split, true);
+      if (ms < 0.f) return CUROB_ERR_CUDA;
+      if (ms < best) {
+        best = ms;
+        b->concurrent = 1;
+        b->grp[0].grid = split[0];
+        b->grp[1].grid = split[1];
+      }
+    }
+  }
+  b->grp[0].order = order[0];
+  b->grp[1].order = order[1];
+  const int g[kGroups] = {b->grp[0].grid, b->grp[1].grid};
   if (cudaStreamBeginCapture(b->priv, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     return CUROB_ERR_CUDA;
-  cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->priv);
-  launch_mma_batch(b->d_args, b->d_work[b->order], b->nwork, b->d_counter, b->grid, b->priv);
-  if (cudaStreamEndCapture(b->priv, &b->graph) != cudaSuccess) return CUROB_ERR_CUDA;
+  const cudaError_t e = issue(b, order, g, b->concurrent != 0);
+  if (cudaStreamEndCapture(b->priv, &b->graph) != cudaSuccess || e != cudaSuccess)
+    return CUROB_ERR_CUDA;
   if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) return CUROB_ERR_CUDA;
   b->tuned = true;
   return CUROB_OK;
@@ -146,8 +235,12 @@ curob_status curob_batch_create(const curob_batch_item* items, int n_items, curo
   curob_batch b = new curob_batch_st();
   cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
   b->items.assign(items, items + n_items);
+  b->grp[0].mode = CUROB_PRECISION_EXACT;
+  b->grp[1].mode = CUROB_PRECISION_TF32X3;
+  b->small.resize(n_items);
   curob_status rc = CUROB_OK;
-  for (const curob_batch_item& it : b->items) {
+  for (int i = 0; i < n_items; ++i) {
+    const curob_batch_item& it = b->items[i];
     auto key = std::make_pair(it.D, it.seed);
     if (!b->inst.count(key)) {
       std::unique_ptr<Instance> I(new Instance());
@@ -156,49 +249,69 @@ curob_status curob_batch_create(const curob_batch_item* items, int n_items, curo
       b->inst[key] = std::move(I);
     }
     Instance* I = b->inst[key].get();
-    if (I->func[it.fid].max_n > mma_max_block()) {
+    const Function& F = I->func[it.fid];
+    if (F.max_n > mma_max_block()) {
       rc = CUROB_ERR_UNSUPPORTED;
       break;
     }
+    // AUTO's precision; MIXED compositions and blocks AUTO leaves to the
+    // CUDA cores go to EXACT
+    const int gi = (mma_supports(I->mma, F) &&
+                    mma_auto_mode(I->mma, F) == CUROB_PRECISION_TF32X3) ? 1 : 0;
     b->item_inst.push_back(I);
-    b->tile_cost.push_back(tile_cost(*I, it.fid));
+    b->item_group.push_back(gi);
+    b->tile_cost.push_back(tile_cost(*I, it.fid, gi));
+    fill_small_args(b->small[i], *I, F);
+    Group& g = b->grp[gi];
+    g.npad_max = std::max(g.npad_max, (F.max_n + 31) / 32 * 32);
   }
   if (rc != CUROB_OK) {
     free_batch(b);
     return rc;
   }
-  // argument blocks and the three candidate work orders
+  // argument blocks (each in its group's precision and stage geometry) and
+  // the three candidate work orders of each group
   const size_t ab = mma_args_bytes();
   std::vector<unsigned char> args(ab * n_items);
   std::vector<int> tiles(n_items);
   for (int i = 0; i < n_items; ++i) {
     const curob_batch_item& it = b->items[i];
     Instance* I = b->item_inst[i];
-    mma_fill_args(args.data() + ab * i, I->mma, I->tables(), I->func[it.fid], it.x, it.out, it.N);
+    Group& g = b->grp[b->item_group[i]];
+    mma_fill_args(args.data() + ab * i, I->mma, I->tables(), I->func[it.fid], it.x, it.out, it.N,
+                  g.mode, g.npad_max);
     tiles[i] = (it.N + 127) / 128;
-    for (int t = 0; t < tiles[i]; ++t) b->work_host[2].push_back(make_int2(i, t));
+    for (int t = 0; t < tiles[i]; ++t) g.work_host[2].push_back(make_int2(i, t));
+    g.cost += b->tile_cost[i] * tiles[i];
   }
-  b->nwork = (int)b->work_host[2].size();
-  b->work_host[0] = b->work_host[2];  // longest tile first
-  std::stable_sort(b->work_host[0].begin(), b->work_host[0].end(),
-                   [&](int2 a, int2 c) { return b->tile_cost[a.x] > b->tile_cost[c.x]; });
+  for (Group& g : b->grp) {
+    g.nwork = (int)g.work_host[2].size();
+    g.work_host[0] = g.work_host[2];  // longest tile first
+    std::stable_sort(g.work_host[0].begin(), g.work_host[0].end(),
+                     [&](int2 a, int2 c) { return b->tile_cost[a.x] > b->tile_cost[c.x]; });
+  }
   for (int t = 0;; ++t) {  // round robin over items
     bool any = false;
     for (int i = 0; i < n_items; ++i)
       if (t < tiles[i]) {
-        b->work_host[1].push_back(make_int2(i, t));
+        b->grp[b->item_group[i]].work_host[1].push_back(make_int2(i, t));
         any = true;
       }
     if (!any) break;
   }
   bool ok = cudaMalloc(&b->d_args, args.size()) == cudaSuccess &&
-            cudaMalloc(&b->d_counter, sizeof(int)) == cudaSuccess &&
-            cudaStreamCreateWithFlags(&b->priv, cudaStreamNonBlocking) == cudaSuccess;
-  for (int o = 0; o < 3 && ok; ++o)
-    ok = cudaMalloc(&b->d_work[o], sizeof(int2) * std::max(b->nwork, 1)) == cudaSuccess &&
-         (b->nwork == 0 || cudaMemcpy(b->d_work[o], b->work_host[o].data(),
-                                      sizeof(int2) * b->nwork, cudaMemcpyHostToDevice) ==
-                               cudaSuccess);
+            cudaStreamCreateWithFlags(&b->priv, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&b->priv2, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) == cudaSuccess;
+  for (Group& g : b->grp) {
+    ok = ok && cudaMalloc(&g.d_counter, sizeof(int)) == cudaSuccess;
+    for (int o = 0; o < 3 && ok; ++o)
+      ok = cudaMalloc(&g.d_work[o], sizeof(int2) * std::max(g.nwork, 1)) == cudaSuccess &&
+           (g.nwork == 0 || cudaMemcpy(g.d_work[o], g.work_host[o].data(),
+                                       sizeof(int2) * g.nwork, cudaMemcpyHostToDevice) ==
+                                cudaSuccess);
+  }
   ok = ok && cudaMemcpy(b->d_args, args.data(), args.size(), cudaMemcpyHostToDevice) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -211,7 +324,7 @@ curob_status curob_batch_create(const curob_batch_item* items, int n_items, curo
 
 curob_status curob_batch_run(curob_batch b, curob_stream_t stream) {
   if (!b) return CUROB_ERR_NULL_POINTER;
-  if (b->nwork == 0) return CUROB_OK;
+  if (b->grp[0].nwork + b->grp[1].nwork == 0) return CUROB_OK;
   if (!b->tuned) {
     curob_status rc = tune_and_capture(b);
     if (rc != CUROB_OK) return rc;
@@ -225,9 +338,34 @@ curob_status curob_batch_run_separate(curob_batch b, curob_stream_t stream) {
     const curob_batch_item& it = b->items[i];
     if (it.N == 0) continue;
     Instance* I = b->item_inst[i];
-    if (launch_mma_fused(I->mma, I->tables(), I->func[it.fid], CUROB_PRECISION_EXACT, it.x,
-                         it.N, it.out, (cudaStream_t)stream) != cudaSuccess)
+    if (launch_mma_fused(I->mma, I->tables(), I->func[it.fid], b->grp[b->item_group[i]].mode,
+                         it.x, it.N, it.out, (cudaStream_t)stream) != cudaSuccess)
       return CUROB_ERR_CUDA;
+  }
+  return CUROB_OK;
+}
+
+curob_status curob_batch_run_auto(curob_batch b, curob_stream_t stream) {
+  if (!b) return CUROB_ERR_NULL_POINTER;
+  const cudaStream_t st = (cudaStream_t)stream;
+  for (size_t i = 0; i < b->items.size(); ++i) {
+    const curob_batch_item& it = b->items[i];
+    if (it.N == 0) continue;
+    Instance* I = b->item_inst[i];
+    const Function& F = I->func[it.fid];
+    cudaError_t e;
+    if (it.N <= kSmallAuto && small_supports(F, I->D)) {
+      e = launch_small_f32(b->small[i], it.x, it.N, it.out, st);
+    } else {
+      const int m = mma_supports(I->mma, F) ? mma_auto_mode(I->mma, F) : CUROB_PRECISION_SIMT;
+      if (m == CUROB_PRECISION_SIMT)
+        e = launch_simt_f32(I->tables(), F, it.x, it.N, it.out, st);
+      else if (m == CUROB_PRECISION_MIXED)
+        e = launch_mma_mixed(I->mma, I->tables(), F, it.x, it.N, it.out, st);
+      else
+        e = launch_mma(I->mma, I->tables(), F, m, it.x, it.N, it.out, st);
+    }
+    if (e != cudaSuccess) return CUROB_ERR_CUDA;
   }
   return CUROB_OK;
 }
@@ -235,9 +373,32 @@ curob_status curob_batch_run_separate(curob_batch b, curob_stream_t stream) {
 curob_status curob_batch_schedule(curob_batch b, int* n_work, int* grid, int* order) {
   if (!b) return CUROB_ERR_NULL_POINTER;
   if (!b->tuned) return CUROB_ERR_NOT_INITIALIZED;
-  if (n_work) *n_work = b->nwork;
-  if (grid) *grid = b->grid;
-  if (order) *order = b->order;
+  const int big = b->grp[1].cost > b->grp[0].cost ? 1 : 0;
+  if (n_work) *n_work = b->grp[0].nwork + b->grp[1].nwork;
+  if (grid)
+    *grid = b->concurrent ? b->grp[0].grid + b->grp[1].grid
+                          : std::max(b->grp[0].nwork ? b->grp[0].grid : 0,
+                                     b->grp[1].nwork ? b->grp[1].grid : 0);
+  if (order) *order = b->grp[big].order;
+  return CUROB_OK;
+}
+
+curob_status curob_batch_plan(curob_batch b, int* items_exact, int* items_tf32, int* work_exact,
+                              int* work_tf32, int* grid_exact, int* grid_tf32, int* order_exact,
+                              int* order_tf32, int* concurrent) {
+  if (!b) return CUROB_ERR_NULL_POINTER;
+  if (!b->tuned) return CUROB_ERR_NOT_INITIALIZED;
+  int ne = 0, nt = 0;
+  for (int gi : b->item_group) (gi ? nt : ne) += 1;
+  if (items_exact) *items_exact = ne;
+  if (items_tf32) *items_tf32 = nt;
+  if (work_exact) *work_exact = b->grp[0].nwork;
+  if (work_tf32) *work_tf32 = b->grp[1].nwork;
+  if (grid_exact) *grid_exact = b->grp[0].nwork ? b->grp[0].grid : 0;
+  if (grid_tf32) *grid_tf32 = b->grp[1].nwork ? b->grp[1].grid : 0;
+  if (order_exact) *order_exact = b->grp[0].order;
+  if (order_tf32) *order_tf32 = b->grp[1].order;
+  if (concurrent) *concurrent = b->concurrent;
   return CUROB_OK;
 }
 

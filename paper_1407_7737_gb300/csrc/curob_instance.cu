@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "curob_instance.hpp"
+#include "curob_small.cuh"
 
 namespace curob {
 namespace {
@@ -466,6 +467,15 @@ curob_status Instance::set_component(int fid, int comp, const double* o, const i
   std::vector<int> ids = ch.segs;
   const curob_status rc = mma_refresh(mma, segs, ids, tables());
   return rc == CUROB_OK ? f64_refresh(f64, segs, ids, tables()) : rc;
+}
+
+void fill_small_args(SmallArgs& a, const Instance& I, const Function& F) {
+  memset(&a, 0, sizeof(a));
+  a.tb = I.tables();
+  a.F = F;
+  a.seg_base = I.comps[F.comp0].seg0;
+  for (int i = 0; i < F.nseg && i < kSmallMaxWarps; ++i) a.seg[i] = I.segs[a.seg_base + i];
+  for (int c = 0; c < F.ncomp; ++c) a.comp[c] = I.comps[F.comp0 + c];
 }
 
 }  // namespace curob

@@ -59,4 +59,8 @@ class Instance {
 
 bool needs_d10(int fid);
 
+// The small-population kernels' by-value copy of a function's segments and
+// components (curob_small.cuh).
+void fill_small_args(SmallArgs& a, const Instance& I, const Function& F);
+
 }  // namespace curob

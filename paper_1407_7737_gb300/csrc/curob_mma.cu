@@ -1947,26 +1947,35 @@ int mma_auto_mode(const MmaPlan& p, const Function& F) {
 }
 
 namespace {
-// Stage geometry of the EXACT persistent kernel (independent of the item).
+// Stage geometry of a persistent launch: EXACT stages hold one N chunk of at
+// most kExactMaxNC columns whatever the item; TF32X3 stages a whole block,
+// sized for the widest block among the launch's items (npad_max).
 struct BatchGeom {
   int nstage, stage_bytes;
   size_t smem;
 };
-BatchGeom batch_geom() {
+template <int kMode>
+BatchGeom batch_geom_t(int npad_max) {
   BatchGeom g;
-  const size_t sb = stage_bytes_for<M_EXACT>(kExactMaxNC);
+  const int ncmax = kMode == M_EXACT ? kExactMaxNC : std::min(kMaxNpad, npad_max);
+  const size_t sb = stage_bytes_for<kMode>(ncmax);
   g.stage_bytes = (int)sb;
   g.nstage = (int)std::min<size_t>(kMaxStages, (kSmemCap - ctrl_bytes()) / sb);
   g.smem = g.nstage * sb + ctrl_bytes() + 1024;
   return g;
+}
+BatchGeom batch_geom(int mode, int npad_max) {
+  return mode == CUROB_PRECISION_TF32X3 ? batch_geom_t<M_TF32>(npad_max)
+                                        : batch_geom_t<M_EXACT>(npad_max);
 }
 }  // namespace
 
 size_t mma_args_bytes() { return sizeof(MmaArgs); }
 
 void mma_fill_args(void* dst, const MmaPlan& p, const Tables& tb, const Function& F,
-                   const float* x, float* out, int N) {
-  const BatchGeom g = batch_geom();
+                   const float* x, float* out, int N, int mode, int npad_max) {
+  const bool tf32 = mode == CUROB_PRECISION_TF32X3;
+  const BatchGeom g = batch_geom(mode, npad_max);
   MmaArgs a;
   a.tb = tb;
   a.F = F;
@@ -1982,26 +1991,29 @@ void mma_fill_args(void* dst, const MmaPlan& p, const Tables& tb, const Function
   a.stage_bytes = g.stage_bytes;
   a.xt = 0;
   a.nA = a.nB = g.nstage;
-  a.a_bytes = MC<M_EXACT>::kParts * MC<M_EXACT>::kPart;
+  a.a_bytes = tf32 ? MC<M_TF32>::kParts * MC<M_TF32>::kPart
+                   : MC<M_EXACT>::kParts * MC<M_EXACT>::kPart;
   a.b_bytes = g.stage_bytes - a.a_bytes;
   a.nlist = F.ncomp;
   for (int i = 0; i < kMaxComponents; ++i) a.list[i] = i;
   a.gout = nullptr;
   a.d2out = nullptr;
   a.zbuf = nullptr;
-  set_acc_regions<M_EXACT>(a, npad_of(F.max_n));
+  if (tf32) set_acc_regions<M_TF32>(a, npad_of(F.max_n));
+  else set_acc_regions<M_EXACT>(a, npad_of(F.max_n));
   memcpy(dst, &a, sizeof(a));
 }
 
 cudaError_t launch_mma_batch(const void* d_args, const int2* d_work, int nwork, int* d_counter,
-                             int grid, cudaStream_t st) {
-  const BatchGeom g = batch_geom();
-  cudaError_t e = cudaFuncSetAttribute(mma_batch_kernel<M_EXACT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+                             int grid, cudaStream_t st, int mode, int npad_max) {
+  const BatchGeom g = batch_geom(mode, npad_max);
+  const auto kern = mode == CUROB_PRECISION_TF32X3 ? mma_batch_kernel<M_TF32>
+                                                   : mma_batch_kernel<M_EXACT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)g.smem);
   if (e != cudaSuccess) return e;
-  mma_batch_kernel<M_EXACT><<<grid, kThreads, g.smem, st>>>(
-      reinterpret_cast<const MmaArgs*>(d_args), d_work, nwork, d_counter, g.nstage,
-      g.stage_bytes);
+  kern<<<grid, kThreads, g.smem, st>>>(reinterpret_cast<const MmaArgs*>(d_args), d_work, nwork,
+                                       d_counter, g.nstage, g.stage_bytes);
   return cudaGetLastError();
 }
 

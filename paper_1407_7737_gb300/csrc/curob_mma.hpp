@@ -53,15 +53,21 @@ cudaError_t launch_mma_fused(const MmaPlan& p, const Tables& tb, const Function&
 // (mode CUROB_PRECISION_MIXED for the latter).
 int mma_launch_count(const Function& F, int mode, int N);
 
-// Persistent EXACT-mode launches over a ragged batch.
+// Persistent launches over a ragged batch, in CUROB_PRECISION_EXACT or
+// _TF32X3 (every item of one launch in the launch's precision).
 size_t mma_args_bytes();
 // Writes the device-side argument block of one batch item into dst (host).
+// npad_max: the widest block (rounded up to 32) among the items of the
+// launch the item belongs to (TF32X3 sizes its stages by it).
 void mma_fill_args(void* dst, const MmaPlan& p, const Tables& tb, const Function& F,
-                   const float* x, float* out, int N);
+                   const float* x, float* out, int N, int mode = CUROB_PRECISION_EXACT,
+                   int npad_max = 512);
 // Launches the persistent kernel on `grid` CTAs over nwork (item, tile)
-// pairs; *d_counter must be 0.
+// pairs; *d_counter must be 0; mode and npad_max as the items' argument
+// blocks were filled with.
 cudaError_t launch_mma_batch(const void* d_args, const int2* d_work, int nwork, int* d_counter,
-                             int grid, cudaStream_t st);
+                             int grid, cudaStream_t st, int mode = CUROB_PRECISION_EXACT,
+                             int npad_max = 512);
 // Largest block width the tensor-core kernels take.
 int mma_max_block();
 

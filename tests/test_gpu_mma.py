@@ -44,6 +44,14 @@ def _sweep(orc, D, N, mode, rows=None, seed=0):
             got = gu.gpu_eval(fid, x32, torch.float32)
             ok, worst, excused, raw = gu.fp32_check(orc, fid, D, seed, x32, got, rows)
             report[fid] = {"ok": ok, "ratio": raw, "excused": excused}
+            if excused:
+                # each excused row: the variable at the jump and the oracle on
+                # both sides of it (printed with -s, saved with the report)
+                from oracle import parity
+                ex = parity.explain_excused(fid, D, seed, x32, got, rows)
+                report[fid]["excused_rows"] = ex
+                for e in ex:
+                    print(f"fid {fid} D {D} mode {mode} excused row {e}")
     finally:
         cu.curob_set_precision(cu.PRECISION_AUTO)
     return report
@@ -73,6 +81,11 @@ def test_auto_precision_parity_full_size(orc):
     _save("mma_auto_D1000.json", rep)
     bad = {f: r for f, r in rep.items() if not r["ok"]}
     assert not bad, bad
+    # every excused row is a jump the FP32 rounding of z crossed: the value
+    # matches the oracle on the other side of that jump
+    crossed = {f: [e for e in r.get("excused_rows", []) if not e["gpu_on_other_side"]]
+               for f, r in rep.items()}
+    assert not any(crossed.values()), crossed
 
 
 @pytest.mark.parametrize("mode", [1, 2, 6])
