@@ -309,8 +309,9 @@ curob_status curob_evaluatef_multi_noalloc(const int* fids, const float* const* 
  * AUTO leaves to the CUDA cores, on EXACT), so every item meets the FP32
  * tolerance; the items of each precision form one persistent launch.  The
  * first curob_batch_run times a few schedules (work order per launch, the two
- * launches in sequence or side by side on a split of the SMs), keeps the
- * fastest, and captures it in a CUDA graph that later runs replay.  A batch
+ * launches in sequence or side by side on a split of the SMs, or every item
+ * on EXACT in one launch), keeps the fastest, and captures it in a CUDA graph
+ * that later runs replay.  A batch
  * owns its instances (one per distinct D, seed); it is independent of
  * curob_initialize.
  * ------------------------------------------------------------------------- */
@@ -338,8 +339,9 @@ curob_status curob_batch_create(const curob_batch_item* items, int n_items, curo
 curob_status curob_batch_run(curob_batch batch, curob_stream_t stream);
 
 /* The same tile arithmetic as one fused launch of the tensor-core kernel per
- * item, in item order, each at its item's precision (values equal to
- * curob_batch_run's bit for bit). */
+ * item, in item order, each at the precision the tuner gave its item (values
+ * equal to curob_batch_run's bit for bit; call it after the first
+ * curob_batch_run). */
 curob_status curob_batch_run_separate(curob_batch batch, curob_stream_t stream);
 
 /* Every item as curob_evaluatef under CUROB_PRECISION_AUTO would evaluate it

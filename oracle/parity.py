@@ -122,13 +122,14 @@ def _mirror(kind, zj):
     return np.copysign(2.0 * jump - a, w) - c
 
 
-def explain_excused(fid, D, seed, x32, got, rows=None, fscale=None):
-    """For each row fp32_check excuses: the discontinuous variable nearest its
-    jump (member, index in the member's z, its z and distance to the jump),
-    the oracle's f at the FP32-rounded x (its FP64 z) and the oracle's f with
-    that one variable reflected to the other side of the jump, and whether the
-    GPU value matches the other side within the FP32 tolerance -- i.e. whether
-    the FP32 rounding of z crossed the jump."""
+def explain_excused(fid, D, seed, x32, got, rows=None, fscale=None, max_vars=12):
+    """For each row fp32_check excuses: the discontinuous variables within the
+    excuse margin of a jump (nearest first, at most max_vars), the oracle's f
+    at the FP32-rounded x (its FP64 z), and the smallest set of those
+    variables which, reflected to the other side of their jumps, gives the GPU
+    value within the FP32 tolerance (found from the single-variable changes,
+    then confirmed by one evaluation with all of them reflected) -- i.e.
+    whether the FP32 rounding of z crossing those jumps explains the value."""
     r = np.arange(x32.shape[0]) if rows is None else np.asarray(rows)
     xr = np.asarray(x32[r], dtype=np.float64)
     ref = oracle.evaluate(fid, D, seed, xr, nthreads=16)
@@ -141,26 +142,47 @@ def explain_excused(fid, D, seed, x32, got, rows=None, fscale=None):
     out = []
     for i in np.nonzero(~ok & edge)[0]:
         x = xr[i]
+        g = float(got[r[i]])
         zs = [oracle.component_z(fid, D, comps, c, x) for c in range(len(comps))]
         d2 = [float(np.sum((x - cc.o) ** 2)) for cc in comps]
-        best = None
+        cand = []  # (relative distance, member, index, kind, distance)
         for comp, block, kind, scale in DISC[fid]:
             sizes = comps[comp].blocks
             lo = 0 if block is None else int(sum(sizes[:block]))
             hi = D if block is None else lo + int(sizes[block])
             dist, v = jump_distance(kind, zs[comp][lo:hi])
             rel = dist / (np.abs(v) + 1.0)
-            j = int(np.argmin(rel))
-            if best is None or rel[j] < best[0]:
-                best = (float(rel[j]), comp, lo + j, kind, float(dist[j]))
-        _, comp, j, kind, dist = best
-        zo = [z.copy() for z in zs]
-        zo[comp][j] = _mirror(kind, zs[comp][j])
-        f_other = oracle.evaluate_from_z(fid, D, zo, d2)
-        out.append({"row": int(r[i]), "gpu": float(got[r[i]]), "oracle": float(ref[i]),
-                    "oracle_other_side": f_other, "tol": float(tol[i]),
-                    "ratio": float(abs(got[r[i]] - ref[i]) / tol[i]),
-                    "member": comp, "z_index": j, "kind": kind, "z": float(zs[comp][j]),
-                    "distance_to_jump": dist,
-                    "gpu_on_other_side": bool(abs(got[r[i]] - f_other) <= tol[i])})
+            for j in np.nonzero(rel <= 1e-5)[0]:
+                cand.append((float(rel[j]), comp, lo + int(j), kind, float(dist[j])))
+        cand.sort()
+        cand = cand[:max_vars]
+
+        def flipped(sel):
+            zo = [z.copy() for z in zs]
+            for (_, comp, j, kind, _) in sel:
+                zo[comp][j] = _mirror(kind, zs[comp][j])
+            return oracle.evaluate_from_z(fid, D, zo, d2)
+
+        delta = np.array([flipped([c]) - ref[i] for c in cand])
+        found = None
+        if cand:
+            n = len(cand)
+            masks = (np.arange(1, 1 << n)[:, None] >> np.arange(n)[None, :]) & 1
+            hit = np.nonzero(np.abs(ref[i] + masks @ delta - g) <= tol[i])[0]
+            for m in hit[np.argsort(masks[hit].sum(axis=1), kind="stable")][:8]:  # smallest sets first
+                sub = tuple(int(k) for k in np.nonzero(masks[m])[0])
+                f_all = flipped([cand[k] for k in sub])
+                if abs(f_all - g) <= tol[i]:
+                    found = (sub, f_all)
+                    break
+        rec = {"row": int(r[i]), "gpu": g, "oracle": float(ref[i]), "tol": float(tol[i]),
+               "ratio": float(abs(g - ref[i]) / tol[i]), "near_jump_variables": len(cand),
+               "gpu_on_other_side": found is not None}
+        if found:
+            sub, f_all = found
+            rec["oracle_other_side"] = f_all
+            rec["crossed"] = [{"member": cand[s][1], "z_index": cand[s][2], "kind": cand[s][3],
+                               "z": float(zs[cand[s][1]][cand[s][2]]),
+                               "distance_to_jump": cand[s][4]} for s in sub]
+        out.append(rec)
     return out

@@ -9,8 +9,9 @@
 // kernel).  The items of each precision form one persistent launch.  The
 // tuner times three work orders per launch on a full grid, then whether the
 // two launches run one after the other or side by side on a split of the SMs
-// (the split from the estimated costs, and its two neighbours), keeps the
-// fastest and captures it in a CUDA graph.
+// (the split from the estimated costs, and its two neighbours), and against
+// them one launch with every item on EXACT (which meets the FP32 bar
+// everywhere); it keeps the fastest and captures it in a CUDA graph.
 #include <algorithm>
 #include <map>
 #include <memory>
@@ -30,7 +31,7 @@ bool device_accessible(const void* p);
 using namespace curob;
 
 namespace {
-constexpr int kGroups = 2;        // 0: EXACT items, 1: TF32X3 items
+constexpr int kGroups = 2;        // 0: EXACT items, 1: TF32X3 items (2: every item on EXACT)
 constexpr int kSmallAuto = 512;   // AUTO's small-population limit (curob_set_small_batch default)
 
 struct Group {
@@ -52,8 +53,10 @@ struct curob_batch_st {
   std::vector<int> item_group;       // 0 EXACT, 1 TF32X3
   std::vector<double> tile_cost;     // estimated cost of one tile of each item
   std::vector<SmallArgs> small;      // per item, for curob_batch_run_auto
-  Group grp[kGroups];
-  void* d_args = nullptr;
+  Group grp[kGroups + 1];
+  void* d_args = nullptr;            // per item, at its group's precision
+  void* d_args_all = nullptr;        // per item, on EXACT (group 2)
+  int all_exact = 0;                 // the tuner chose group 2
   int nsm = 0;
   bool tuned = false;
   int concurrent = 0;
@@ -97,6 +100,7 @@ void free_batch(curob_batch b) {
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->join) cudaEventDestroy(b->join);
   cudaFree(b->d_args);
+  cudaFree(b->d_args_all);
   for (Group& g : b->grp) {
     for (int o = 0; o < 3; ++o) cudaFree(g.d_work[o]);
     cudaFree(g.d_counter);
@@ -109,13 +113,16 @@ cudaError_t launch_group(curob_batch b, int gi, int order, int grid, cudaStream_
   Group& g = b->grp[gi];
   cudaError_t e = cudaMemsetAsync(g.d_counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  return launch_mma_batch(b->d_args, g.d_work[order], g.nwork, g.d_counter,
+  return launch_mma_batch(gi == kGroups ? b->d_args_all : b->d_args, g.d_work[order], g.nwork,
+                          g.d_counter,
                           std::min(grid, std::max(1, g.nwork)), st, g.mode, g.npad_max);
 }
 
 // Issues a schedule on b->priv: the groups in sequence, or side by side (the
 // TF32X3 group on priv2, forked from and joined back into priv).
-cudaError_t issue(curob_batch b, const int* order, const int* grid, bool concurrent) {
+cudaError_t issue(curob_batch b, const int* order, const int* grid, bool concurrent,
+                  int all_order = -1) {
+  if (all_order >= 0) return launch_group(b, kGroups, all_order, b->nsm, b->priv);
   const bool both = b->grp[0].nwork > 0 && b->grp[1].nwork > 0;
   cudaError_t e = cudaSuccess;
   if (concurrent && both) {
@@ -133,14 +140,15 @@ cudaError_t issue(curob_batch b, const int* order, const int* grid, bool concurr
 }
 
 // Time one schedule (ms): two runs, the second measured.
-float time_schedule(curob_batch b, const int* order, const int* grid, bool concurrent) {
+float time_schedule(curob_batch b, const int* order, const int* grid, bool concurrent,
+                    int all_order = -1) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float ms = -1.f;
   for (int rep = 0; rep < 2; ++rep) {
     cudaEventRecord(e0, b->priv);
-    if (issue(b, order, grid, concurrent) != cudaSuccess) {
+    if (issue(b, order, grid, concurrent, all_order) != cudaSuccess) {
       ms = -1.f;
       break;
     }
@@ -198,10 +206,25 @@ curob_status tune_and_capture(curob_batch b) {
   }
   b->grp[0].order = order[0];
   b->grp[1].order = order[1];
+  // every item on EXACT, one launch
+  b->all_exact = 0;
+  if (b->grp[1].nwork > 0) {
+    for (int o = 0; o < 3; ++o) {
+      const float ms = time_schedule(b, order, grid, false, o);
+      if (ms < 0.f) return CUROB_ERR_CUDA;
+      if (ms < best) {
+        best = ms;
+        b->all_exact = 1;
+        b->grp[kGroups].order = o;
+        b->grp[kGroups].grid = b->nsm;
+      }
+    }
+  }
   const int g[kGroups] = {b->grp[0].grid, b->grp[1].grid};
   if (cudaStreamBeginCapture(b->priv, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     return CUROB_ERR_CUDA;
-  const cudaError_t e = issue(b, order, g, b->concurrent != 0);
+  const cudaError_t e = issue(b, order, g, b->concurrent != 0,
+                              b->all_exact ? b->grp[kGroups].order : -1);
   if (cudaStreamEndCapture(b->priv, &b->graph) != cudaSuccess || e != cudaSuccess)
     return CUROB_ERR_CUDA;
   if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) return CUROB_ERR_CUDA;
@@ -284,6 +307,14 @@ curob_status curob_batch_create(const curob_batch_item* items, int n_items, curo
     for (int t = 0; t < tiles[i]; ++t) g.work_host[2].push_back(make_int2(i, t));
     g.cost += b->tile_cost[i] * tiles[i];
   }
+  {  // group 2: every item on EXACT, same tiles
+    Group& g = b->grp[kGroups];
+    g.mode = CUROB_PRECISION_EXACT;
+    for (int i = 0; i < n_items; ++i) {
+      for (int t = 0; t < tiles[i]; ++t) g.work_host[2].push_back(make_int2(i, t));
+      g.cost += tile_cost(*b->item_inst[i], b->items[i].fid, 0) * tiles[i];
+    }
+  }
   for (Group& g : b->grp) {
     g.nwork = (int)g.work_host[2].size();
     g.work_host[0] = g.work_host[2];  // longest tile first
@@ -295,9 +326,17 @@ curob_status curob_batch_create(const curob_batch_item* items, int n_items, curo
     for (int i = 0; i < n_items; ++i)
       if (t < tiles[i]) {
         b->grp[b->item_group[i]].work_host[1].push_back(make_int2(i, t));
+        b->grp[kGroups].work_host[1].push_back(make_int2(i, t));
         any = true;
       }
     if (!any) break;
+  }
+  std::vector<unsigned char> args_all(ab * n_items);
+  for (int i = 0; i < n_items; ++i) {
+    const curob_batch_item& it = b->items[i];
+    Instance* I = b->item_inst[i];
+    mma_fill_args(args_all.data() + ab * i, I->mma, I->tables(), I->func[it.fid], it.x, it.out,
+                  it.N, CUROB_PRECISION_EXACT, b->grp[kGroups].npad_max);
   }
   bool ok = cudaMalloc(&b->d_args, args.size()) == cudaSuccess &&
             cudaStreamCreateWithFlags(&b->priv, cudaStreamNonBlocking) == cudaSuccess &&
@@ -313,6 +352,9 @@ curob_status curob_batch_create(const curob_batch_item* items, int n_items, curo
                                 cudaSuccess);
   }
   ok = ok && cudaMemcpy(b->d_args, args.data(), args.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->d_args_all, args_all.size()) == cudaSuccess &&
+       cudaMemcpy(b->d_args_all, args_all.data(), args_all.size(), cudaMemcpyHostToDevice) ==
+           cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     free_batch(b);
@@ -324,7 +366,7 @@ curob_status curob_batch_create(const curob_batch_item* items, int n_items, curo
 
 curob_status curob_batch_run(curob_batch b, curob_stream_t stream) {
   if (!b) return CUROB_ERR_NULL_POINTER;
-  if (b->grp[0].nwork + b->grp[1].nwork == 0) return CUROB_OK;
+  if (b->grp[kGroups].nwork == 0) return CUROB_OK;
   if (!b->tuned) {
     curob_status rc = tune_and_capture(b);
     if (rc != CUROB_OK) return rc;
@@ -338,8 +380,9 @@ curob_status curob_batch_run_separate(curob_batch b, curob_stream_t stream) {
     const curob_batch_item& it = b->items[i];
     if (it.N == 0) continue;
     Instance* I = b->item_inst[i];
-    if (launch_mma_fused(I->mma, I->tables(), I->func[it.fid], b->grp[b->item_group[i]].mode,
-                         it.x, it.N, it.out, (cudaStream_t)stream) != cudaSuccess)
+    const int mode = b->all_exact ? CUROB_PRECISION_EXACT : b->grp[b->item_group[i]].mode;
+    if (launch_mma_fused(I->mma, I->tables(), I->func[it.fid], mode, it.x, it.N, it.out,
+                         (cudaStream_t)stream) != cudaSuccess)
       return CUROB_ERR_CUDA;
   }
   return CUROB_OK;
@@ -373,12 +416,13 @@ curob_status curob_batch_run_auto(curob_batch b, curob_stream_t stream) {
 curob_status curob_batch_schedule(curob_batch b, int* n_work, int* grid, int* order) {
   if (!b) return CUROB_ERR_NULL_POINTER;
   if (!b->tuned) return CUROB_ERR_NOT_INITIALIZED;
-  const int big = b->grp[1].cost > b->grp[0].cost ? 1 : 0;
-  if (n_work) *n_work = b->grp[0].nwork + b->grp[1].nwork;
+  const int big = b->all_exact ? kGroups : (b->grp[1].cost > b->grp[0].cost ? 1 : 0);
+  if (n_work) *n_work = b->grp[kGroups].nwork;
   if (grid)
-    *grid = b->concurrent ? b->grp[0].grid + b->grp[1].grid
-                          : std::max(b->grp[0].nwork ? b->grp[0].grid : 0,
-                                     b->grp[1].nwork ? b->grp[1].grid : 0);
+    *grid = b->all_exact ? b->grp[kGroups].grid
+            : b->concurrent ? b->grp[0].grid + b->grp[1].grid
+                            : std::max(b->grp[0].nwork ? b->grp[0].grid : 0,
+                                       b->grp[1].nwork ? b->grp[1].grid : 0);
   if (order) *order = b->grp[big].order;
   return CUROB_OK;
 }
@@ -389,16 +433,18 @@ curob_status curob_batch_plan(curob_batch b, int* items_exact, int* items_tf32, 
   if (!b) return CUROB_ERR_NULL_POINTER;
   if (!b->tuned) return CUROB_ERR_NOT_INITIALIZED;
   int ne = 0, nt = 0;
-  for (int gi : b->item_group) (gi ? nt : ne) += 1;
+  for (int gi : b->item_group) (gi && !b->all_exact ? nt : ne) += 1;
+  const Group& ge = b->grp[b->all_exact ? kGroups : 0];
+  const Group& gt = b->grp[1];
   if (items_exact) *items_exact = ne;
   if (items_tf32) *items_tf32 = nt;
-  if (work_exact) *work_exact = b->grp[0].nwork;
-  if (work_tf32) *work_tf32 = b->grp[1].nwork;
-  if (grid_exact) *grid_exact = b->grp[0].nwork ? b->grp[0].grid : 0;
-  if (grid_tf32) *grid_tf32 = b->grp[1].nwork ? b->grp[1].grid : 0;
-  if (order_exact) *order_exact = b->grp[0].order;
-  if (order_tf32) *order_tf32 = b->grp[1].order;
-  if (concurrent) *concurrent = b->concurrent;
+  if (work_exact) *work_exact = ge.nwork;
+  if (work_tf32) *work_tf32 = b->all_exact ? 0 : gt.nwork;
+  if (grid_exact) *grid_exact = ge.nwork ? ge.grid : 0;
+  if (grid_tf32) *grid_tf32 = (!b->all_exact && gt.nwork) ? gt.grid : 0;
+  if (order_exact) *order_exact = ge.order;
+  if (order_tf32) *order_tf32 = gt.order;
+  if (concurrent) *concurrent = b->all_exact ? 0 : b->concurrent;
   return CUROB_OK;
 }
 

@@ -41,7 +41,8 @@ def test_excused_row_lies_across_the_jump():
     assert ok and excused == 1 and raw > 1
     rep = parity.explain_excused(7, D, 0, x32, got)
     assert len(rep) == 1 and rep[0]["row"] == 1
-    assert rep[0]["gpu_on_other_side"] and rep[0]["member"] == 0 and rep[0]["z_index"] == 0
+    assert rep[0]["gpu_on_other_side"]
+    assert [(c["member"], c["z_index"]) for c in rep[0]["crossed"]] == [(0, 0)]
     # a value that is simply wrong is not on the other side
     got[1] = ref[1] + 7.0
     rep = parity.explain_excused(7, D, 0, x32, got)
@@ -57,3 +58,27 @@ def test_mirror_reflects_across_the_jump():
     z = -1500.0 - c - 2e-9
     zm = parity._mirror("schwefel", z)
     assert abs((zm + c) + (1500.0 - 2e-9)) < 1e-9
+
+
+def test_two_crossed_jumps():
+    """Two Step variables at their jumps, the GPU value on the other side of
+    both: the explanation names both."""
+    D = 10
+    comps = oracle.generate(7, D, 0)
+    c = comps[0]
+    x = inputs.uniform(2, D, 5)
+    z = oracle.component_z(7, D, comps, 0, x[0])
+    n0 = c.blocks[0]
+    y = (0.5 - 2e-7 - z[0]) * c.R[0][0, :] + (-1.5 + 3e-7 - z[1]) * c.R[0][1, :]
+    x[0, c.S[:n0]] += y
+    x32 = x.astype(np.float32)
+    ref = oracle.evaluate(7, D, 0, x32.astype(np.float64))
+    zs = oracle.component_z(7, D, comps, 0, x32[0].astype(np.float64))
+    zo = zs.copy()
+    zo[0] = parity._mirror("step", zs[0])
+    zo[1] = parity._mirror("step", zs[1])
+    got = ref.copy()
+    got[0] = oracle.evaluate_from_z(7, D, [zo])
+    rep = parity.explain_excused(7, D, 0, x32, got)
+    assert len(rep) == 1 and rep[0]["gpu_on_other_side"]
+    assert sorted(v["z_index"] for v in rep[0]["crossed"]) == [0, 1]
