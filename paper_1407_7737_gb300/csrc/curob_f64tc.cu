@@ -41,6 +41,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "curob_f64tc.hpp"
@@ -489,6 +490,117 @@ constexpr int kFinArr = 3;    // term arrays of a kind (f64_num_terms <= 3)
 constexpr int kFinTile = kFinArr * kFinCols * 32;  // doubles of one tile
 constexpr size_t kFinSmem = 2 * kFinTile * sizeof(double);  // 48 KB
 
+// Katsuura's inner sum (Sec. 4.11) sum_{j=1}^{32} |2^j z - [2^j z]| / 2^j,
+// exact: with z = +-m 2^q (m the 53-bit significand), 2^j |z| has t = -(q + j)
+// fraction bits, its distance to the nearest integer is min(r, 2^t - r) 2^-t
+// (r its low t bits of m), and divided by 2^j every term is an integer
+// multiple of 2^q.  The sum is therefore S 2^q with S < 2^58, formed in
+// integer arithmetic and rounded once -- the same value as the series added
+// term by term, up to the additions' roundings (a few ulps).
+__device__ __forceinline__ double katsuura_inner_exact(double z) {
+  const long long b = __double_as_longlong(z);
+  const int be = (int)((b >> 52) & 0x7ff);
+  if (be == 0x7ff) return z - z;          // non-finite: NaN, as the series gives
+  if (be == 0) return 32.0 * fabs(z);     // zero or subnormal: every term is |z|
+  const long long m = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+  const int q = be - 1075;
+  unsigned long long S = 0;
+#pragma unroll 4
+  for (int j = 1; j <= 32; ++j) {
+    const int t = -(q + j);
+    if (t <= 0) break;                    // 2^j |z| and every later one are integers
+    if (t >= 54) {
+      S += (unsigned long long)m;         // 2^j |z| < 1/2
+    } else {
+      const unsigned long long one = 1ull << t;
+      const unsigned long long r = (unsigned long long)m & (one - 1ull);
+      S += r < one - r ? r : one - r;
+    }
+  }
+  return ldexp((double)S, q);
+}
+
+// Weierstrass inner sum of the FP64 path (Sec. 4.2), the value of
+// weierstrass_inner(double): sum_{k=0}^{20} 2^-k cos(x_k) with
+// x_k = fl(c_k w), c_k = fl(P 3^k), P = 2 fl(pi) and w = fl(z + 1/2) -- the
+// rounded arguments of the printed expression -- but with each cosine from an
+// exact reduction instead of the library's:
+//   c_k w = x_k + d_k exactly (d_k by one fma), and P 3^k = c_k + e_k exactly,
+//   P = 2 pi - eta, so x_k = 2 pi 3^k w - (eta 3^k + e_k) w - d_k: modulo 2 pi
+//   it is 2 pi F_k - G_k w - d_k, F_k = frac(3^k w) formed exactly from w's
+//   significand in 128-bit integer arithmetic, G_k = eta 3^k + e_k (a
+//   constant, |G_k w + d_k| < 2e-5).  F_k is centred on the nearest quarter
+//   turn Q/4, leaving |theta| <= pi/4 + 2e-5 (theta to ~1e-17 in double), and
+//   cos(x_k) = +-cos(theta) or +-sin(theta) by Q from Taylor series to
+//   theta^16 / theta^17 (truncation below 2e-17).
+constexpr double kEta = 2.4492935982947064e-16;  // 2 pi - 2 fl(pi), to double precision
+struct WeierK {
+  double c, g;  // c_k = fl(P 3^k); G_k = eta 3^k + e_k
+};
+__constant__ WeierK c_weier[21];
+
+// cos(theta) (odd = 0) or sin(theta) (odd = 1), |theta| <= ~0.8, without a
+// branch (the parity differs from lane to lane): cos = 1 + u Pc(u) and
+// sin = theta + theta u Ps(u), u = theta^2, Pc and Ps the Taylor series to
+// theta^16 and theta^17 (coefficients 1/n! by correctly rounded division),
+// one Horner chain on per-lane selected coefficients.
+__device__ __forceinline__ double cos_or_sin_small(double th, bool odd) {
+  const double u = th * th;
+  double p = odd ? 1.0 / 355687428096000.0 : 1.0 / 20922789888000.0;  // 1/17!, 1/16!
+  p = fma(p, u, odd ? -1.0 / 1307674368000.0 : -1.0 / 87178291200.0);  // 1/15!, 1/14!
+  p = fma(p, u, odd ? 1.0 / 6227020800.0 : 1.0 / 479001600.0);         // 1/13!, 1/12!
+  p = fma(p, u, odd ? -1.0 / 39916800.0 : -1.0 / 3628800.0);           // 1/11!, 1/10!
+  p = fma(p, u, odd ? 1.0 / 362880.0 : 1.0 / 40320.0);                 // 1/9!, 1/8!
+  p = fma(p, u, odd ? -1.0 / 5040.0 : -1.0 / 720.0);                   // 1/7!, 1/6!
+  p = fma(p, u, odd ? 1.0 / 120.0 : 1.0 / 24.0);                       // 1/5!, 1/4!
+  p = fma(p, u, odd ? -1.0 / 6.0 : -0.5);                              // 1/3!, 1/2!
+  const double base = odd ? th : 1.0;
+  return fma(p * u, base, base);
+}
+
+// -v for flip, v otherwise (the sign bit, no arithmetic).
+__device__ __forceinline__ double flip_sign(double v, bool flip) {
+  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)flip << 63));
+}
+
+__device__ __forceinline__ double weierstrass_inner_exact(double z) {
+  const double w = z + 0.5;
+  const long long b = __double_as_longlong(w);
+  const int be = (int)((b >> 52) & 0x7ff);
+  const int s = 1075 - be;  // fraction bits of w's significand
+  // |w| in [2^-9, 2^50): s in [3, 62], where 3^k m mod 2^s is the low s bits
+  // of the 64-bit product; other w (far outside the box) take the series
+  if (be == 0 || s < 3 || s > 62) return weierstrass_inner(z);
+  const unsigned long long m = (unsigned long long)((b & 0xFFFFFFFFFFFFFLL) | (1LL << 52));
+  const bool neg = b < 0;
+  const unsigned long long mask = (1ull << s) - 1ull;
+  const unsigned long long half_q = 1ull << (s - 3);   // an eighth turn
+  const unsigned long long quart = (1ull << (s - 2)) - 1ull;
+  const double scale = __longlong_as_double((long long)(1023 - s) << 52);  // 2^-s
+  double acc = 0.0, ak = 1.0;
+  unsigned long long p3 = 1;  // 3^k
+#pragma unroll 3
+  for (int k = 0; k <= 20; ++k) {
+    const WeierK K = c_weier[k];
+    const double x = K.c * w;                            // the printed expression's argument
+    const double corr = fma(K.g, w, fma(K.c, w, -x));    // G_k w + d_k
+    // F = frac(3^k |w|) (the low s bits of 3^k m), centred on the nearest quarter turn
+    const unsigned long long u = ((m * p3) & mask) + half_q;
+    int Q = (int)(u >> (s - 2)) & 3;
+    // frac(-v) = -frac(v)
+    const double F = flip_sign((double)((long long)(u & quart) - (long long)half_q) * scale, neg);
+    if (neg) Q = (4 - Q) & 3;
+    // theta = 2 pi F - corr, 2 pi = P + eta
+    const double hi = (2.0 * kPi) * F;
+    const double th = hi + (fma(kEta, F, fma(2.0 * kPi, F, -hi)) - corr);
+    const double v = cos_or_sin_small(th, Q & 1);       // cos(theta + Q pi/2), up to sign
+    acc += ak * flip_sign(v, Q == 1 || Q == 2);
+    ak *= 0.5;
+    p3 *= 3ull;
+  }
+  return acc;
+}
+
 // The terms of one warp's columns of a chunk, with the kind fixed at compile
 // time (a kind known only at run time inside the loop lets the compiler
 // form other kinds' transcendentals for every variable).
@@ -507,6 +619,13 @@ __device__ __forceinline__ void fin64_terms(double* T, const double* zb, long lo
             (gpos + j > 0)
                 ? pair_term<double>(KIND, zb[(long long)(j - 1) * N], zb[(long long)j * N])
                 : 0.0;
+      } else if constexpr (KIND == K_WEIERSTRASS) {
+        T[jc * 32 + lane] = weierstrass_inner_exact(zb[(long long)j * N]);
+      } else if constexpr (KIND == K_KATSUURA) {
+        // log of the factor 1 + (i+1) s_i: the function's product of the
+        // factors' powers is formed as exp(e * sum log) at its last block
+        const double zj = zb[(long long)j * N];
+        T[jc * 32 + lane] = log(1.0 + (double)(gpos + j + 1) * katsuura_inner_exact(zj));
       } else {
         const double zj = zb[(long long)j * N];
         const double av = aux ? aux[j] : 0.0;
@@ -584,7 +703,7 @@ __global__ void __launch_bounds__(kFinWarps * 32, 2) f64_finish_kernel(Tables tb
           } else {
             for (int q2 = 0; q2 < na; ++q2) {
               const double* t = T + q2 * kFinCols * 32 + lane;
-              if (f64_term_is_product(kind, q2)) {
+              if (f64_term_is_product(kind, q2) && kind != K_KATSUURA) {
                 for (int jc = 0; jc < ncol; ++jc) p *= t[jc * 32];
               } else if (q2 == 0) {
                 for (int jc = 0; jc < ncol; ++jc) {
@@ -602,6 +721,10 @@ __global__ void __launch_bounds__(kFinWarps * 32, 2) f64_finish_kernel(Tables tb
             if (kind_is_cyclic(kind)) {  // (z_gn, z_1) closes the cycle
               const double* zf = zc + (long long)(sg.zoff - sg.gpos) * N;
               a0 += pair_term<double>(kind, zf[(long long)(sg.gn - 1) * N], zf[0]);
+            }
+            if (kind == K_KATSUURA) {  // prod_i (1 + (i+1) s_i)^e = exp(e sum log)
+              p = exp(kat_e * a0);
+              a0 = 0.0;
             }
             gsum += finalize(kind, a0, a1, a2, p, sg.gn);
           }
@@ -783,7 +906,15 @@ curob_status f64_prepare(F64Plan& p, const std::vector<Segment>& segs,
       f64_release(p);
       return rc;
     }
-    if (cudaFuncSetAttribute(f64_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    WeierK wk[21];
+    double bk = 1.0;
+    for (int k = 0; k <= 20; ++k, bk *= 3.0) {
+      wk[k].c = (2.0 * kPi) * bk;                           // as the FP64 path rounds it
+      const double e = std::fma(2.0 * kPi, bk, -wk[k].c);    // P 3^k - c_k, exact
+      wk[k].g = std::fma(kEta, bk, e);
+    }
+    if (cudaMemcpyToSymbol(c_weier, wk, sizeof(wk)) != cudaSuccess ||
+        cudaFuncSetAttribute(f64_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)mma_smem_bytes()) != cudaSuccess) {
       f64_release(p);
       return CUROB_ERR_CUDA;
