@@ -53,8 +53,10 @@ def test_paper_protocol_calls_match_oracle(orc, D):
 @pytest.mark.parametrize("D,N", [(2, 7), (11, 1), (32, 200), (96, 512), (120, 33)])
 def test_small_equals_batched_kernels(orc, D, N):
     """The same calls with the small kernels turned off: the FP64 values are
-    identical bit for bit, the FP32 ones within the FP32 tolerance of each
-    other and of the oracle."""
+    identical bit for bit to the batched FP64-pipe kernel (same fma order and
+    index-order sums) and within the FP64 bar of the tensor-core FP64 path,
+    the FP32 ones within the FP32 tolerance of each other and of the
+    oracle."""
     import torch
     cu = gu.ensure(D, N)
     try:
@@ -68,10 +70,14 @@ def test_small_equals_batched_kernels(orc, D, N):
             a32 = cu.evaluate(fid, x32)
             cu.curob_set_small_batch(0)
             assert not cu.curob_query_small(fid, N)
+            cu.curob_set_precision64(cu.PRECISION64_SIMT)
             b64 = cu.evaluate(fid, xt)
+            cu.curob_set_precision64(cu.PRECISION64_AUTO)
+            t64 = cu.evaluate(fid, xt)  # tensor-core FP64 path
             b32 = cu.evaluate(fid, x32)
             torch.cuda.synchronize()
             assert torch.equal(a64, b64), (fid, (a64 - b64).abs().max().item())
+            assert ((t64 - a64).abs() <= 1e-12 * a64.abs()).all(), fid
             got = a32.cpu().numpy().astype(np.float64)
             ok, worst, excused, raw = gu.fp32_check(orc, fid, D, 0, x32.cpu().numpy(), got)
             assert ok, (fid, raw)
@@ -80,6 +86,7 @@ def test_small_equals_batched_kernels(orc, D, N):
             assert ok2.all() or fid in (7, 15, 16), fid
     finally:
         cu.curob_set_small_batch(512)
+        cu.curob_set_precision64(cu.PRECISION64_AUTO)
 
 
 def test_small_limit_and_queries():
