@@ -64,6 +64,9 @@ def parse():
                          "FP64, against the oracle on one core): one JSON line, no benchmark line")
     ap.add_argument("--profile-fid", type=int, default=None,
                     help="profiling case: two launches of one function, no JSON")
+    ap.add_argument("--profile-fp64", type=str, default=None,
+                    help="profiling case of curob_evaluate (FP64 tensor-core path): two calls of "
+                         "each listed function ('all' or comma-separated IDs), no JSON")
     return ap.parse_args()
 
 
@@ -392,7 +395,7 @@ def run_curob(args):
 
     # 37 FP32 batches, resident in HBM before timing starts (one for a
     # profiling case)
-    nb = NFUN if args.profile_fid is None else 1
+    nb = NFUN if (args.profile_fid is None and args.profile_fp64 is None) else 1
     X = torch.empty((nb, N, D), dtype=torch.float32, device=dev)
     g = torch.Generator(device=dev)
     g.manual_seed(1234 + rank)
@@ -403,6 +406,18 @@ def run_curob(args):
     if args.profile_fid is not None:
         for _ in range(2):
             cu.curob_evaluatef(args.profile_fid, X[0], N, OUT[0], stream)
+        torch.cuda.synchronize()
+        cu.curob_get_device_status(stream)
+        cu.curob_dispose()
+        return
+    if args.profile_fp64 is not None:
+        fids = (list(range(NFUN)) if args.profile_fp64 == "all"
+                else [int(v) for v in args.profile_fp64.split(",")])
+        x64 = X[0].double()
+        o64 = torch.empty(N, dtype=torch.float64, device=dev)
+        for fid in fids:
+            for _ in range(2):
+                cu.curob_evaluate(fid, x64, N, o64, stream)
         torch.cuda.synchronize()
         cu.curob_get_device_status(stream)
         cu.curob_dispose()

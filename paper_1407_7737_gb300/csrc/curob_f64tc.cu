@@ -30,11 +30,12 @@
 //                      digit image of the candidates' tile (the exact shared-
 //                      memory layout of the MMA's A operand), ||x - o||^2 of
 //                      the block; unrotated blocks write z = y + c directly;
-//   f64_mma_kernel     one CTA per (tile of 128 candidates, chunk of <= 80
-//                      output columns of a block): warp 0 loads the A and B
-//                      digit images of each K step with bulk copies, warp 1
-//                      issues the 28 MMAs per step, warps 2..9 drain the
-//                      exact classes after every K chunk and write z;
+//   f64_mma_kernel     persistent, one CTA per SM over the units (tile of 128
+//                      candidates, chunk of <= 80 output columns of a block):
+//                      warp 0 loads the A and B digit images of each K step
+//                      with bulk copies, warp 1 issues the 28 MMAs per step,
+//                      warps 2..9 drain the exact classes after every K chunk
+//                      and write z;
 //   f64_finish_kernel  the FP64 terms of every variable (the expressions of
 //                      the FP64 path), the sums of each basic function, its
 //                      closing map and the composition (Sec. 6).
@@ -305,12 +306,17 @@ struct MmaArgs64 {
   double* z;                // [component][D][N]
   int* status;
   int nchunks, KS, N, D;
+  int nunits;               // tiles x chunks
 };
 
-// One CTA per (tile, chunk); see the file comment.  TMEM columns: class k
-// (0..4) at k * 80, classes 5 and 6 at 400.  Every wait is bounded: past
-// ~2 s it raises DEV_TIMEOUT, the roles stop, copies and MMAs in flight are
-// waited for (again bounded) and TMEM is freed before the CTA exits.
+// Persistent: CTA b takes the units (tile, chunk) b, b + gridDim.x, ... in
+// order (unit u = tile * nchunks + chunk, so the CTAs working at one time
+// share their tiles' A images in L2).  The operand ring and the accumulator
+// hand-off run on across units: the loader fetches the next unit's K steps
+// while the epilogue drains the last one.  TMEM columns: class k (0..4) at
+// k * 80, classes 5 and 6 at 400.  Every wait is bounded: past ~2 s it
+// raises DEV_TIMEOUT, the roles stop, copies and MMAs in flight are waited
+// for (again bounded) and TMEM is freed before the CTA exits.
 __global__ void __launch_bounds__(kMmaThreads, 1) f64_mma_kernel(const MmaArgs64 a) {
   extern __shared__ uint8_t smem_dyn[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -325,11 +331,6 @@ __global__ void __launch_bounds__(kMmaThreads, 1) f64_mma_kernel(const MmaArgs64
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int unit = blockIdx.x;
-  const int tile = unit / a.nchunks;
-  const F64Chunk ch = a.chunks[unit - tile * a.nchunks];
-  const int nk = ch.nk;
-  const int nkc = (nk + kKChunkSteps - 1) / kKChunkSteps;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -350,54 +351,76 @@ __global__ void __launch_bounds__(kMmaThreads, 1) f64_mma_kernel(const MmaArgs64
 
   if (warp == 0) {
     if (lane == 0) {  // loader
-      const uint8_t* A = a.aimg + ((long long)tile * a.KS + ch.ksg) * kABytes;
-      const uint8_t* B = a.bimg + ch.b_off;
-      const uint32_t bbytes = (uint32_t)ch.nwc * kDigits * 32;
-      int t = 0;
-      for (; t < nk; ++t) {
-        const int s = t % kStages;
-        if (t >= kStages && !mbar_wait(&empty[s], ((t / kStages) - 1) & 1, abort_flag, a.status))
-          break;
-        uint8_t* st = smem + s * kStageStride;
-        mbar_arrive_expect_tx(&full[s], kABytes + bbytes);
-        bulk_g2s(st, A + (long long)t * kABytes, kABytes, &full[s]);
-        bulk_g2s(st + kABytes, B + (long long)t * bbytes, bbytes, &full[s]);
+      uint32_t g = 0;  // K steps issued
+      bool ok = true;
+      for (int unit = blockIdx.x; unit < a.nunits && ok; unit += gridDim.x) {
+        const int tile = unit / a.nchunks;
+        const F64Chunk ch = a.chunks[unit - tile * a.nchunks];
+        const uint8_t* A = a.aimg + ((long long)tile * a.KS + ch.ksg) * kABytes;
+        const uint8_t* B = a.bimg + ch.b_off;
+        const uint32_t bbytes = (uint32_t)ch.nwc * kDigits * 32;
+        for (int t = 0; t < ch.nk; ++t, ++g) {
+          const int s = g % kStages;
+          if (g >= kStages && !mbar_wait(&empty[s], ((g / kStages) - 1) & 1, abort_flag, a.status)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = smem + s * kStageStride;
+          mbar_arrive_expect_tx(&full[s], kABytes + bbytes);
+          bulk_g2s(st, A + (long long)t * kABytes, kABytes, &full[s]);
+          bulk_g2s(st + kABytes, B + (long long)t * bbytes, bbytes, &full[s]);
+        }
       }
       // no copy may still be landing when the CTA exits
       const unsigned long long deadline = globaltimer() + kTimeoutNs;
-      for (int u = max(0, t - kStages); u < t; ++u)
-        mbar_drain(&full[u % kStages], (uint32_t)(u / kStages) & 1u, deadline);
+      for (uint32_t v = g > (uint32_t)kStages ? g - kStages : 0; v < g; ++v)
+        mbar_drain(&full[v % kStages], (v / kStages) & 1u, deadline);
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
-      const uint32_t idesc = idesc_make(1u, 128u, (uint32_t)ch.nwc);
-      for (int t = 0; t < nk; ++t) {
-        const int s = t % kStages;
-        const int kc = t / kKChunkSteps;
-        const bool first = (t % kKChunkSteps) == 0;
-        if (first && kc > 0 && !mbar_wait(tempty, (uint32_t)(kc - 1) & 1u, abort_flag, a.status))
-          break;
-        if (!mbar_wait(&full[s], (uint32_t)(t / kStages) & 1u, abort_flag, a.status)) break;
-        tc_fence_after();
-        const uint32_t abase = smem_u32(smem + s * kStageStride);
-        const uint32_t bbase = abase + kABytes;
+      uint32_t g = 0, c = 0;  // K steps consumed, K chunks handed to the epilogue
+      bool ok = true;
+      for (int unit = blockIdx.x; unit < a.nunits && ok; unit += gridDim.x) {
+        const int tile = unit / a.nchunks;
+        const F64Chunk ch = a.chunks[unit - tile * a.nchunks];
+        const uint32_t idesc = idesc_make(1u, 128u, (uint32_t)ch.nwc);
+        for (int t = 0; t < ch.nk; ++t, ++g) {
+          const int s = g % kStages;
+          const bool first = (t % kKChunkSteps) == 0;
+          // the previous K chunk (of this unit or the last) has been drained
+          if (first && c > 0 && !mbar_wait(tempty, (c - 1) & 1u, abort_flag, a.status)) {
+            ok = false;
+            break;
+          }
+          if (!mbar_wait(&full[s], (g / kStages) & 1u, abort_flag, a.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t abase = smem_u32(smem + s * kStageStride);
+          const uint32_t bbase = abase + kABytes;
 #pragma unroll
-        for (int k = 0; k < kDigits; ++k) {  // classes 0..6: digit pairs (ai, k - ai)
-          const uint32_t dcol = tmem + (uint32_t)(k < kExactClasses ? k : kExactClasses) * kF64Nw;
+          for (int k = 0; k < kDigits; ++k) {  // classes 0..6: digit pairs (ai, k - ai)
+            const uint32_t dcol =
+                tmem + (uint32_t)(k < kExactClasses ? k : kExactClasses) * kF64Nw;
 #pragma unroll
-          for (int ai = 0; ai <= k; ++ai) {
-            const int bi = k - ai;
-            const uint64_t ad = sdesc_sw32(abase + ai * kASlice);
-            const uint64_t bd = sdesc_sw32(bbase + bi * ch.nwc * 32);
-            // the first product of an exact class in a K chunk, and of the
-            // tail in the block, overwrites its accumulator
-            const bool fresh = (k < kExactClasses) ? (first && ai == 0)
-                                                   : (t == 0 && k == kExactClasses && ai == 0);
-            tc_mma<false>(dcol, ad, bd, idesc, fresh ? 0u : 1u);
+            for (int ai = 0; ai <= k; ++ai) {
+              const int bi = k - ai;
+              const uint64_t ad = sdesc_sw32(abase + ai * kASlice);
+              const uint64_t bd = sdesc_sw32(bbase + bi * ch.nwc * 32);
+              // the first product of an exact class in a K chunk, and of the
+              // tail in the unit, overwrites its accumulator
+              const bool fresh = (k < kExactClasses) ? (first && ai == 0)
+                                                     : (t == 0 && k == kExactClasses && ai == 0);
+              tc_mma<false>(dcol, ad, bd, idesc, fresh ? 0u : 1u);
+            }
+          }
+          tc_commit(&empty[s]);
+          if ((t % kKChunkSteps) == kKChunkSteps - 1 || t == ch.nk - 1) {
+            tc_commit(tfull);
+            ++c;
           }
         }
-        tc_commit(&empty[s]);
-        if ((t % kKChunkSteps) == kKChunkSteps - 1 || t == nk - 1) tc_commit(tfull);
       }
       tc_commit(done);
       mbar_drain(done, 0, globaltimer() + kTimeoutNs);
@@ -407,61 +430,80 @@ __global__ void __launch_bounds__(kMmaThreads, 1) f64_mma_kernel(const MmaArgs64
     const int quarter = warp & 3;  // a warp reads TMEM lanes 32 (warp % 4) .. + 31
     const int half = ew >> 2;      // columns [40 half, 40 half + 40)
     const int m = quarter * 32 + lane;
-    const long long row = (long long)tile * kTile + m;
-    const bool valid = row < a.N;
     const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
-    const int em = valid ? a.sexp[(long long)ch.sslot * a.N + row] : 0;
-    long long W[40];
+    uint32_t c = 0;  // K chunks drained
+    bool ok = true;
+    for (int unit = blockIdx.x; unit < a.nunits && ok; unit += gridDim.x) {
+      const int tile = unit / a.nchunks;
+      const F64Chunk ch = a.chunks[unit - tile * a.nchunks];
+      const int nkc = (ch.nk + kKChunkSteps - 1) / kKChunkSteps;
+      const long long row = (long long)tile * kTile + m;
+      const bool valid = row < a.N;
+      const int em = valid ? a.sexp[(long long)ch.sslot * a.N + row] : 0;
+      long long W[40];
+      float T[40];  // classes 5 and 6, read at the unit's last K chunk
 #pragma unroll
-    for (int i = 0; i < 40; ++i) W[i] = 0;
-    for (int kc = 0; kc < nkc; ++kc) {
-      const bool ok = mbar_wait(tfull, (uint32_t)kc & 1u, abort_flag, a.status);
-      if (!__all_sync(0xffffffffu, ok)) break;
-      tc_fence_after();
-      const bool last = kc == nkc - 1;
+      for (int i = 0; i < 40; ++i) W[i] = 0;
+      for (int kc = 0; kc < nkc; ++kc, ++c) {
+        const bool got = mbar_wait(tfull, c & 1u, abort_flag, a.status);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const bool last = kc == nkc - 1;
 #pragma unroll
-      for (int g = 0; g < 5; ++g) {
-        const int col0 = half * 40 + g * 8;
-        if (col0 < ch.nwc) {  // warp-uniform; nwc is a multiple of 16
-          uint32_t r[kExactClasses + 1][8];
+        for (int gq = 0; gq < 5; ++gq) {
+          const int col0 = half * 40 + gq * 8;
+          if (col0 < ch.nwc) {  // warp-uniform; nwc is a multiple of 16
+            uint32_t r[kExactClasses + 1][8];
 #pragma unroll
-          for (int k = 0; k < kExactClasses; ++k) tmem_ld8(taddr + k * kF64Nw + col0, r[k]);
-          if (last) tmem_ld8(taddr + kExactClasses * kF64Nw + col0, r[kExactClasses]);
-          tmem_wait_ld();
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            // class k holds C_k 2^-8k, |C_k| <= 2^24: exact integers once scaled
-            long long w = (long long)__float2int_rn(__uint_as_float(r[0][i])) << 32;
-            w += (long long)__float2int_rn(__uint_as_float(r[1][i]) * 256.f) << 24;
-            w += (long long)__float2int_rn(__uint_as_float(r[2][i]) * 65536.f) << 16;
-            w += (long long)__float2int_rn(__uint_as_float(r[3][i]) * 16777216.f) << 8;
-            w += (long long)__float2int_rn(__uint_as_float(r[4][i]) * 4294967296.f);
-            W[g * 8 + i] += w;
-          }
-          if (last && valid) {
+            for (int k = 0; k < kExactClasses; ++k) tmem_ld8(taddr + k * kF64Nw + col0, r[k]);
+            if (last) tmem_ld8(taddr + kExactClasses * kF64Nw + col0, r[kExactClasses]);
+            tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              const int col = col0 + i;
-              if (col < ch.nvalid) {
-                const long long tf =
-                    __float2ll_rn(__uint_as_float(r[kExactClasses][i]) * 281474976710656.f);
-                const __int128 X = ((__int128)W[g * 8 + i] << 16) + tf;
-                double zv;
-                if (em == kExpNonFinite) {
-                  zv = __longlong_as_double(0x7FF8000000000000LL);
-                } else {
-                  zv = i128_to_double(X, em + a.rexp[ch.rexp_off + col] - 62);
-                  if (ch.offset != 0.0) zv = zv + ch.offset;
+              // class k holds C_k 2^-8k, |C_k| <= 2^24: exact integers once scaled
+              long long w = (long long)__float2int_rn(__uint_as_float(r[0][i])) << 32;
+              w += (long long)__float2int_rn(__uint_as_float(r[1][i]) * 256.f) << 24;
+              w += (long long)__float2int_rn(__uint_as_float(r[2][i]) * 65536.f) << 16;
+              w += (long long)__float2int_rn(__uint_as_float(r[3][i]) * 16777216.f) << 8;
+              w += (long long)__float2int_rn(__uint_as_float(r[4][i]) * 4294967296.f);
+              W[gq * 8 + i] += w;
+              if (last) T[gq * 8 + i] = __uint_as_float(r[kExactClasses][i]);
+            }
+          }
+        }
+        // TMEM is read: hand it back, so the next K chunk (or unit) runs
+        // under the conversions below
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty);
+        if (last && valid) {
+#pragma unroll
+          for (int gq = 0; gq < 5; ++gq) {
+            const int col0 = half * 40 + gq * 8;
+            if (col0 < ch.nwc) {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const int col = col0 + i;
+                if (col < ch.nvalid) {
+                  const long long tf = __float2ll_rn(T[gq * 8 + i] * 281474976710656.f);
+                  const __int128 X = ((__int128)W[gq * 8 + i] << 16) + tf;
+                  double zv;
+                  if (em == kExpNonFinite) {
+                    zv = __longlong_as_double(0x7FF8000000000000LL);
+                  } else {
+                    zv = i128_to_double(X, em + a.rexp[ch.rexp_off + col] - 62);
+                    if (ch.offset != 0.0) zv = zv + ch.offset;
+                  }
+                  a.z[((long long)ch.comp * a.D + ch.zcol + col) * a.N + row] = zv;
                 }
-                a.z[((long long)ch.comp * a.D + ch.zcol + col) * a.N + row] = zv;
               }
             }
           }
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(tempty);
     }
   }
   tc_fence_before();
@@ -900,6 +942,7 @@ curob_status f64_prepare(F64Plan& p, const std::vector<Segment>& segs,
   }
   std::vector<int> all(nseg);
   for (size_t s = 0; s < nseg; ++s) all[s] = (int)s;
+  cudaDeviceGetAttribute(&p.nsm, cudaDevAttrMultiProcessorCount, dev);
   if (cc_major == 10) {  // the digit images feed tcgen05: built where it runs
     const curob_status rc = build_rimg(p, segs, all, tb);
     if (rc != CUROB_OK) {
@@ -977,7 +1020,9 @@ cudaError_t launch_f64tc(const F64Plan& p, cudaMemPool_t pool, const Tables& tb,
       a.KS = p.ks_total[fid];
       a.N = ns;
       a.D = D;
-      f64_mma_kernel<<<ntiles * (unsigned)p.nchunk[fid], kMmaThreads, mma_smem_bytes(), st>>>(a);
+      a.nunits = (int)ntiles * p.nchunk[fid];
+      const unsigned grid = (unsigned)std::min(a.nunits, std::max(p.nsm, 1));
+      f64_mma_kernel<<<grid, kMmaThreads, mma_smem_bytes(), st>>>(a);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {

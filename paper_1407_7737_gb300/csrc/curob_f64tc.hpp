@@ -38,6 +38,7 @@ struct F64Plan {
   int ks_total[kNumFunctions] = {};  // K steps over them
   std::vector<long long> seg_img;    // host copies: per segment, digit image offset (-1 none)
   std::vector<long long> seg_rexp;   // per segment, first row exponent
+  int nsm = 0;                       // persistent grid of the tensor-core launch
   bool ready = false;
 };
 
