@@ -175,28 +175,35 @@ __global__ void f64_rimg_kernel(const RImgJob* jobs, const double* R, const int*
 // becomes NaN (non-finite inputs give NaN outputs).
 constexpr int kExpNonFinite = 0x7fffffff;
 
-// One thread per candidate (row of the tile) and segment of F (blockIdx.y).
-// Rotated blocks: pass 1 finds max_j |y_j| through max_j |x_j - o_j| (the
-// rounded product s d is monotone in |d|), pass 2 writes the seven digit
-// slices of each K step of 16 variables in the 32-byte-swizzled K-major
-// layout of the MMA's A operand (a warp writes 32 consecutive rows).
-// Unrotated blocks write z = s (x - o) + c straight into the z scratch
-// ([component][variable][N], candidates inner).  Both leave the block's
-// share of ||x - o||^2 (compositions) in d2p[segment][N].
-__global__ void __launch_bounds__(kTile) f64_prep_kernel(Tables tb, Function F,
-                                                         const int2* __restrict__ seginfo,
-                                                         const double* __restrict__ x, int N,
-                                                         int KS, uint8_t* __restrict__ aimg,
-                                                         int* __restrict__ sexp,
-                                                         double* __restrict__ z,
-                                                         double* __restrict__ d2p) {
+// A block takes 32 candidates (the lanes; a quarter of a 128-row tile) and
+// one segment of F (blockIdx.y); warp g of 4 takes every fourth variable of
+// the block (pass 1, unrotated blocks) and every fourth K step (pass 2), so
+// each candidate has four threads.  Rotated blocks: pass 1 finds max_j |y_j|
+// through max_j |x_j - o_j| (the rounded product s d is monotone in |d|),
+// pass 2 writes the seven digit slices of each K step of 16 variables in the
+// 32-byte-swizzled K-major layout of the MMA's A operand (a warp writes 32
+// consecutive rows).  Unrotated blocks write z = s (x - o) + c straight into
+// the z scratch ([component][variable][N], candidates inner).  Both leave the
+// block's share of ||x - o||^2 (compositions) in d2p[segment][N], the four
+// warps' parts added in warp order.
+constexpr int kPrepRows = 32;
+constexpr int kPrepWarps = 4;
+
+__global__ void __launch_bounds__(kPrepRows * kPrepWarps) f64_prep_kernel(
+    Tables tb, Function F, const int2* __restrict__ seginfo, const double* __restrict__ x, int N,
+    int KS, uint8_t* __restrict__ aimg, int* __restrict__ sexp, double* __restrict__ z,
+    double* __restrict__ d2p) {
+  __shared__ long long mxs[kPrepWarps][kPrepRows];
+  __shared__ double d2s[kPrepWarps][kPrepRows];
   const int seg0 = tb.comp[F.comp0].seg0;
   const int si = blockIdx.y;
   const Segment sg = tb.seg[seg0 + si];
   const int c = sg.comp - F.comp0;
   const Component C = tb.comp[sg.comp];
-  const int m = threadIdx.x;
-  const long long row = (long long)blockIdx.x * kTile + m;
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int tile = blockIdx.x / (kTile / kPrepRows);
+  const int m = (blockIdx.x % (kTile / kPrepRows)) * kPrepRows + lane;  // row in the tile
+  const long long row = (long long)tile * kTile + m;
   const bool valid = row < N;
   const int D = tb.D;
   const int* __restrict__ S = tb.S + C.base + sg.zoff;
@@ -209,7 +216,7 @@ __global__ void __launch_bounds__(kTile) f64_prep_kernel(Tables tb, Function F,
   if (info.x < 0) {
     if (valid) {
       double* zc = z + ((long long)c * D + sg.zoff) * N + row;
-      for (int j = 0; j < n; ++j) {
+      for (int j = g; j < n; j += kPrepWarps) {
         const double d = xr[S[j]] - op[j];
         if (want_d2) d2 += d * d;
         const double y = sg.scale * d;
@@ -219,18 +226,21 @@ __global__ void __launch_bounds__(kTile) f64_prep_kernel(Tables tb, Function F,
   } else {
     long long mb = 0;  // bits of max_j |x_j - o_j| (non-negative doubles order as integers)
     if (valid)
-      for (int j = 0; j < n; ++j) {
+      for (int j = g; j < n; j += kPrepWarps) {
         const double d = xr[S[j]] - op[j];
         if (want_d2) d2 += d * d;
         mb = max(mb, __double_as_longlong(d) & 0x7FFFFFFFFFFFFFFFLL);
       }
+    mxs[g][lane] = mb;
+    __syncthreads();
+    mb = max(max(mxs[0][lane], mxs[1][lane]), max(mxs[2][lane], mxs[3][lane]));
     const bool finite = mb < 0x7FF0000000000000LL;
     const int e = finite ? f64_scale_exp(fabs(sg.scale) * __longlong_as_double(mb)) : 0;
-    if (valid) sexp[(long long)info.x * N + row] = finite ? e : kExpNonFinite;
+    if (valid && g == 0) sexp[(long long)info.x * N + row] = finite ? e : kExpNonFinite;
     const int nk = (n + 15) / 16;
-    uint8_t* at = aimg + ((long long)blockIdx.x * KS + info.y) * kABytes;
+    uint8_t* at = aimg + ((long long)tile * KS + info.y) * kABytes;
     const bool live = valid && finite;
-    for (int t = 0; t < nk; ++t) {
+    for (int t = g; t < nk; t += kPrepWarps) {
       uint32_t w[kDigits][8];
 #pragma unroll
       for (int a = 0; a < kDigits; ++a)
@@ -257,7 +267,12 @@ __global__ void __launch_bounds__(kTile) f64_prep_kernel(Tables tb, Function F,
       }
     }
   }
-  if (valid && want_d2) d2p[(long long)si * N + row] = d2;
+  if (want_d2) {
+    d2s[g][lane] = d2;
+    __syncthreads();
+    if (valid && g == 0)
+      d2p[(long long)si * N + row] = ((d2s[0][lane] + d2s[1][lane]) + d2s[2][lane]) + d2s[3][lane];
+  }
 }
 
 // ------------------------------------------------------------- MMA kernel
@@ -1004,7 +1019,8 @@ cudaError_t launch_f64tc(const F64Plan& p, cudaMemPool_t pool, const Tables& tb,
     double* d2p = reinterpret_cast<double*>(b + L.d2p);
     const double* xs = x + s0 * D;
     const unsigned ntiles = (unsigned)((ns + kTile - 1) / kTile);
-    f64_prep_kernel<<<dim3(ntiles, (unsigned)F.nseg), kTile, 0, st>>>(
+    f64_prep_kernel<<<dim3(ntiles * (kTile / kPrepRows), (unsigned)F.nseg), kPrepRows * kPrepWarps,
+                      0, st>>>(
         tb, F, p.seginfo, xs, ns, p.ks_total[fid], aimg, sexp, zs, d2p);
     e = cudaGetLastError();
     if (e == cudaSuccess && p.nchunk[fid] > 0) {
