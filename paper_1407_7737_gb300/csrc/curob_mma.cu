@@ -85,6 +85,7 @@ constexpr int kCtrlHeader = 512;                 // barrier header of the contro
 constexpr size_t kSmemCap = 227 * 1024 - 1024;   // dynamic shared memory, less alignment slack
 constexpr int kExactAcc1 = 256;                  // EXACT: TMEM column of accumulator 1
 constexpr int kSigRing = 8;                      // EXACT: row scales in flight
+constexpr size_t kTabTBytes = 2 * kMaxNpad * sizeof(float);  // epilogue's tau buffers
 
 enum Mode : int { M_TF32 = 0, M_BF16 = 1, M_EXACT = 2, M_F16 = 3 };
 // Modes whose operands are scaled per row: y by sigma_m (a power of two above
@@ -168,6 +169,15 @@ struct MmaArgs {
   // drained before the next hand-off may start.
   int acc_hi;
   int acc_ovl;
+  // Scaled modes: 1 when the launch reserved kTabTBytes past the control
+  // block, where the epilogue stages each block's tau (else it reads them
+  // from global memory).
+  int tabt;
+  // Scaled modes: per component, the row maxima max_j |x_j - o_j| in
+  // partial form ([ntx][pm_ld] floats each: one partial per 64 variables,
+  // written by the transpose of x); nullptr: the producers form them.
+  const float* rowpm;
+  int ntx, pm_ld;
 };
 
 // The allocation-free entry point keeps up to 64 argument blocks in 32 KB.
@@ -352,6 +362,9 @@ struct Smem {
   float* rowMx;  // EXACT: max_j |x_j - o_j| of each row
   int* tabS;
   float *tabH, *tabL;
+  float* tabT;         // scaled modes: the epilogue's row scales tau of R, two blocks
+                       // (past the control block; MmaArgs::tabt says it exists)
+  uint64_t* epi_bar;   // the 4 epilogue warps
   int* item;  // persistent kernel: the work item of the CTA
 };
 
@@ -400,6 +413,7 @@ __device__ inline Smem smem_map(uint8_t* smem_raw, const RingGeom& g) {
     m.emptyB = m.empty;
     m.rawfull = nullptr;
   }
+  m.epi_bar = next++;
   m.tmem_slot = reinterpret_cast<uint32_t*>(next);
   m.abort_flag = reinterpret_cast<volatile int*>(m.tmem_slot + 1);
   m.item = const_cast<int*>(reinterpret_cast<volatile int*>(m.abort_flag) + 1);
@@ -410,6 +424,7 @@ __device__ inline Smem smem_map(uint8_t* smem_raw, const RingGeom& g) {
   m.tabS = reinterpret_cast<int*>(m.rowMx + kTileM);              // [kMaxNpad]
   m.tabH = reinterpret_cast<float*>(m.tabS + kMaxNpad);
   m.tabL = m.tabH + kMaxNpad;
+  m.tabT = m.tabL + kMaxNpad;   // [2][kMaxNpad], only where the launch reserved it (MmaArgs::tabt)
   return m;
 }
 
@@ -421,6 +436,8 @@ struct RoleState {
   uint32_t comp_it = 0;   // components (row-scale ring)
   uint32_t b_par = 0;     // B loads: bit s = parity of stage s's last load, bit 8 + s = used
   uint32_t r_par = 0;     // raw gathers (xt), the same bookkeeping per A slot
+  uint32_t e_blk = 0;     // epilogue: blocks staged (tabT buffer parity)
+  uint32_t e_phase = 0;   // epilogue group barrier uses
 };
 
 __device__ inline void cta_setup(const Smem& m, int xt) {
@@ -441,6 +458,7 @@ __device__ inline void cta_setup(const Smem& m, int xt) {
     mbar_init(m.tmem_empty, 4);   // the 4 epilogue warps
     for (int s = 0; s < kSigRing; ++s) mbar_init(&m.sig_full[s], 4);  // producer warps 0-3
     mbar_init(m.prod_bar, 8);     // the 8 producer warps
+    mbar_init(m.epi_bar, 4);      // the 4 epilogue warps
     *m.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -570,7 +588,19 @@ __device__ void producer_tile(const MmaArgs& a, const Smem& m, long long row0, R
       // ||x - o||^2 only feeds the composition weights
       const bool need_d2 = F.composition != 0 || a.d2out != nullptr;
       float isig = 1.f;
-      if constexpr (scaled_mode(kMode)) {
+      if (scaled_mode(kMode) && a.rowpm) {
+        // max_j |x_j - o_j| of each row over the component from the
+        // transpose's partial maxima (one per 64 variables), read after the
+        // next producer barrier
+        if (h == 0) {
+          float mv = 0.f;
+          if (vrow) {
+            const float* pp = a.rowpm + (size_t)ci * a.ntx * a.pm_ld + grow;
+            for (int t = 0; t < a.ntx; ++t) mv = fmaxf(mv, __ldg(pp + (size_t)t * a.pm_ld));
+          }
+          m.rowMx[r] = mv;
+        }
+      } else if constexpr (scaled_mode(kMode)) {
         // max_j |x_j - o_j| of each row over the component, read in natural
         // order: half h of the warp pair reads rows 16 h .. 16 h + 15 of the
         // pair's 32 with coalesced loads (o as FP32); the maxima meet in
@@ -1020,6 +1050,22 @@ __device__ void epilogue_tile(const MmaArgs& a, const Smem& m, long long row0, R
         es.gpos = sg.gpos;
         es.gfirst = sg.gfirst;
         const float* tau = a.tau + sg.tau_off;
+        // scaled modes: the block's row scales of R go to shared memory once
+        // (every drained column needs one, the same for all 128 rows), in one
+        // of two buffers: a warp stages the next block only after its own
+        // drain of this one, and the group barrier then holds it until every
+        // warp has finished this block
+        const float* tt = a.tabt ? m.tabT + (rs.e_blk & 1u) * kMaxNpad : tau;
+        if (scaled_mode(kMode) && a.tabt) {
+          float* tw = m.tabT + (rs.e_blk & 1u) * kMaxNpad;
+          for (int k = r; k < sg.npad; k += kTileM) tw[k] = k < sg.n ? __ldg(tau + k) : 0.f;
+          if (!producers_sync(m.epi_bar, rs.e_phase, abort_flag, tb.status)) {
+            ok = false;
+            break;
+          }
+        }
+        ++rs.e_blk;
+        (void)tau;
         // heavy kinds with a z scratch: the rows' z go out, variable-major
         // (a warp's store of one variable covers 32 consecutive rows)
         const bool zout = a.zbuf != nullptr && sg.hoff >= 0;
@@ -1051,11 +1097,11 @@ __device__ void epilogue_tile(const MmaArgs& a, const Smem& m, long long row0, R
                 const float base = sig * 6.103515625e-05f;  // sigma 2^-14
 #pragma unroll
                 for (int k = 0; k < 32; ++k)
-                  v[k] = (k < cend) ? (v[k] + g1[k]) * (base * tau[c + k]) : 0.f;
+                  v[k] = (k < cend) ? (v[k] + g1[k]) * (base * tt[c + k]) : 0.f;
               } else if constexpr (kMode == M_F16) {
                 tmem_ld32(t_lane + ab + (uint32_t)l, v);
 #pragma unroll
-                for (int k = 0; k < 32; ++k) v[k] = (k < cend) ? v[k] * (sig * tau[c + k]) : 0.f;
+                for (int k = 0; k < 32; ++k) v[k] = (k < cend) ? v[k] * (sig * tt[c + k]) : 0.f;
               } else {
                 tmem_ld32(t_lane + ab + (uint32_t)l, v);
               }
@@ -1110,9 +1156,24 @@ __device__ void mma_tile(const MmaArgs& a, const Smem& m, long long row0, RoleSt
   CUROB_ROLE_PROLOGUE
   (void)row0;
     // ------------------------------------------------------------ MMA issue
+    // One thread issues every MMA of the CTA, so its own instructions between
+    // two stages are time the tensor pipe may stand idle: the descriptors of
+    // the rings' first slots are formed once (a descriptor's address field is
+    // the byte address / 16, so a slot, part or K step is a constant added to
+    // it), and slot indices and barrier parities advance by counting.
     if (lane == 0) {
       uint32_t& it = rs.it;
       uint32_t& chunk_it = rs.chunk_it;
+      const bool split_b = m.fullB != m.full;
+      const int nA = m.nA, nB = m.nB;
+      int sA = (int)(it % (uint32_t)nA), sB = (int)(it % (uint32_t)nB);
+      uint32_t pA = (it / (uint32_t)nA) & 1u, pB = (it / (uint32_t)nB) & 1u;
+      const uint64_t dA0 = sdesc_m<kMode>(smem_u32(m.a_base));
+      const uint64_t dB0 = sdesc_m<kMode>(smem_u32(m.b_base));
+      const uint32_t aStr = (uint32_t)m.a_stride >> 4, bStr = (uint32_t)m.b_stride >> 4;
+      uint32_t offA = (uint32_t)sA * aStr, offB = (uint32_t)sB * bStr;
+      constexpr uint32_t kPart16 = (uint32_t)kPart >> 4;
+      constexpr uint32_t kKo16 = (uint32_t)(C::kMmaK * kEl) >> 4;  // one MMA K step
       bool ok = true;
       for (int li = 0; li < a.nlist && ok && !*abort_flag; ++li) {
         const Component Cm = tb.comp[F.comp0 + a.list[li]];
@@ -1127,30 +1188,29 @@ __device__ void mma_tile(const MmaArgs& a, const Smem& m, long long row0, RoleSt
             const int n1 = nc - n0;
             const uint32_t id0 = idesc_make(C::kFmt, kTileM, (uint32_t)n0);
             const uint32_t id1 = idesc_make(C::kFmt, kTileM, (uint32_t)(n1 > 0 ? n1 : 16));
+            const uint32_t bpart16 = (uint32_t)(nc * kRow) >> 4;  // B part, in 16-byte units
+            const uint32_t bh16 = (uint32_t)(n0 * kRow) >> 4;     // second N range of a part
             if (!mbar_wait(tmem_empty, (chunk_it & 1u) ^ 1u, abort_flag, tb.status)) {
               ok = false;
               break;
             }
             tc_fence_after();
             const uint32_t ab = (chunk_it & 1u) ? (uint32_t)a.acc_hi : 0u;  // accumulator region
+            const uint32_t dt0 = tmem_base + ab, dt1 = dt0 + (uint32_t)n0;
             for (int t = 0; t < nslab; ++t, ++it) {
-              const int sA = it % m.nA, sB = it % m.nB;
-              if (!mbar_wait(&full[sA], (it / m.nA) & 1u, abort_flag, tb.status)) {
+              if (!mbar_wait(&full[sA], pA, abort_flag, tb.status)) {
                 ok = false;
                 break;
               }
-              if (m.fullB != m.full &&
-                  !mbar_wait(&m.fullB[sB], (it / m.nB) & 1u, abort_flag, tb.status)) {
+              if (split_b && !mbar_wait(&m.fullB[sB], pB, abort_flag, tb.status)) {
                 ok = false;
                 break;
               }
               tc_fence_after();
-              const uint32_t sa = smem_u32(m.a_base + (size_t)sA * m.a_stride);
-              const uint32_t sb = smem_u32(m.b_base + (size_t)sB * m.b_stride);
-              const uint32_t bpart = (uint32_t)(nc * kRow);
+              const uint64_t da = dA0 + offA, db = dB0 + offB;
 #pragma unroll
               for (int kk = 0; kk < kKsteps; ++kk) {
-                const uint32_t ko = (uint32_t)(kk * C::kMmaK * kEl);  // bytes per K step
+                const uint32_t ko = (uint32_t)kk * kKo16;
                 const uint32_t first = (t == 0 && kk == 0) ? 0u : 1u;
                 if constexpr (kMode == M_EXACT) {
                   // s1 r1 into accumulator 0; the pre-scaled products of
@@ -1158,27 +1218,40 @@ __device__ void mma_tile(const MmaArgs& a, const Smem& m, long long row0, RoleSt
                   constexpr int kPa[10] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
                   constexpr int kPb[10] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
 #pragma unroll
-                  for (int pq = 0; pq < 10; ++pq) {
-                    const uint32_t dt = tmem_base + ab + (pq == 0 ? 0u : (uint32_t)kExactAcc1);
-                    const uint64_t da = sdesc_m<kMode>(sa + kPa[pq] * kPart + ko);
-                    const uint64_t db = sdesc_m<kMode>(sb + kPb[pq] * bpart + ko);
-                    tc_mma<false>(dt, da, db, id0, (pq <= 1) ? first : 1u);
-                  }
+                  for (int pq = 0; pq < 10; ++pq)
+                    tc_mma<false>(pq == 0 ? dt0 : dt0 + (uint32_t)kExactAcc1,
+                                  da + (uint32_t)kPa[pq] * kPart16 + ko,
+                                  db + (uint32_t)kPb[pq] * bpart16 + ko, id0,
+                                  (pq <= 1) ? first : 1u);
                 } else {
-                  const uint64_t dah = sdesc_m<kMode>(sa + ko), dal = sdesc_m<kMode>(sa + kPart + ko);
-                  for (int h = 0; h < (n1 > 0 ? 2 : 1); ++h) {
-                    const uint32_t boff = (uint32_t)(h * n0 * kRow) + ko;
-                    const uint64_t dbh = sdesc_m<kMode>(sb + boff), dbl = sdesc_m<kMode>(sb + bpart + boff);
-                    const uint32_t dt = tmem_base + ab + (uint32_t)(h * n0);
-                    const uint32_t idd = h ? id1 : id0;
-                    tc_mma<kMode == M_TF32>(dt, dah, dbh, idd, first);
-                    tc_mma<kMode == M_TF32>(dt, dah, dbl, idd, 1u);
-                    tc_mma<kMode == M_TF32>(dt, dal, dbh, idd, 1u);
+                  const uint64_t dah = da + ko, dal = da + kPart16 + ko;
+                  const uint64_t dbh = db + ko, dbl = db + bpart16 + ko;
+                  tc_mma<kMode == M_TF32>(dt0, dah, dbh, id0, first);
+                  tc_mma<kMode == M_TF32>(dt0, dah, dbl, id0, 1u);
+                  tc_mma<kMode == M_TF32>(dt0, dal, dbh, id0, 1u);
+                  if (n1 > 0) {
+                    tc_mma<kMode == M_TF32>(dt1, dah, dbh + bh16, id1, first);
+                    tc_mma<kMode == M_TF32>(dt1, dah, dbl + bh16, id1, 1u);
+                    tc_mma<kMode == M_TF32>(dt1, dal, dbh + bh16, id1, 1u);
                   }
                 }
               }
               tc_commit(&empty[sA]);  // frees the stage when these MMAs retire
-              if (m.emptyB != m.empty) tc_commit(&m.emptyB[sB]);
+              if (split_b) tc_commit(&m.emptyB[sB]);
+              if (++sA == nA) {
+                sA = 0;
+                offA = 0;
+                pA ^= 1u;
+              } else {
+                offA += aStr;
+              }
+              if (++sB == nB) {
+                sB = 0;
+                offB = 0;
+                pB ^= 1u;
+              } else {
+                offB += bStr;
+              }
             }
             if (ok) tc_commit(tmem_full);  // this chunk's accumulators complete
           }
@@ -1696,6 +1769,8 @@ void set_acc_regions(MmaArgs& a, int npad_max) {
 struct XtView {
   const float* xt = nullptr;
   const CUtensorMap* map = nullptr;
+  const float* pm = nullptr;  // partial row maxima per component (MmaArgs::rowpm), or nullptr
+  int ntx = 0, pm_ld = 0;
 };
 
 template <int kMode>
@@ -1735,6 +1810,12 @@ cudaError_t launch_mode(const MmaPlan& p, const Tables& tb, const Function& F, c
       smem = nA * ab + nB * bb + ctrl + 1024;
     }
   }
+  // the epilogue's tau buffers, where they fit beside the rings
+  a.tabt = scaled_mode(kMode) && smem - 1024 + kTabTBytes <= kSmemCap ? 1 : 0;
+  if (a.tabt) smem += kTabTBytes;
+  a.rowpm = scaled_mode(kMode) ? xv.pm : nullptr;
+  a.ntx = xv.ntx;
+  a.pm_ld = xv.pm_ld;
   a.tb = tb;
   a.F = F;
   a.x = x;
@@ -1769,8 +1850,17 @@ cudaError_t launch_mode(const MmaPlan& p, const Tables& tb, const Function& F, c
 // tiles through shared memory, read and written 16 bytes per thread and
 // access (both sides coalesced).  Needs D % 4 == 0 and 16-byte aligned x;
 // otherwise transpose_x_scalar_kernel.
+// Row maxima the scaled modes need (MmaArgs::rowpm): for each listed
+// component q, max_j |x_j - o_j| over each block's 64 variables, o in FP32 in
+// natural order, the producers' own expression; pm[q][blockIdx.x][row].
+struct RowMaxJob {
+  int nc = 0;
+  const float* o[kMaxComponents];
+  float* pm[kMaxComponents];
+};
 __global__ void __launch_bounds__(256) transpose_x_kernel(const float* __restrict__ x, int N,
-                                                          int D, float* __restrict__ xt, int ld) {
+                                                          int D, float* __restrict__ xt, int ld,
+                                                          RowMaxJob job) {
   __shared__ float tile[64][65];
   const int c0 = blockIdx.x * 64;  // variables
   const int r0 = blockIdx.y * 64;  // candidates
@@ -1783,6 +1873,18 @@ __global__ void __launch_bounds__(256) transpose_x_kernel(const float* __restric
     tile[k][4 * tx + 1] = v.y;
     tile[k][4 * tx + 2] = v.z;
     tile[k][4 * tx + 3] = v.w;
+#pragma unroll
+    for (int q = 0; q < kMaxComponents; ++q) {  // the 16 lanes of a half-warp hold row r's 64 variables
+      if (q >= job.nc) break;
+      float mv = 0.f;
+      if (c < D) {
+        const float4 w = __ldg(reinterpret_cast<const float4*>(job.o[q] + c));
+        mv = fmaxf(fmaxf(fabsf(v.x - w.x), fabsf(v.y - w.y)), fmaxf(fabsf(v.z - w.z), fabsf(v.w - w.w)));
+      }
+#pragma unroll
+      for (int off = 8; off > 0; off >>= 1) mv = fmaxf(mv, __shfl_xor_sync(0xffffffffu, mv, off));
+      if (tx == 0 && r < ld) job.pm[q][(size_t)blockIdx.x * ld + r] = r < N ? mv : 0.f;
+    }
   }
   __syncthreads();
   for (int k = ty; k < 64; k += 16) {
@@ -1808,10 +1910,15 @@ __global__ void transpose_x_scalar_kernel(const float* __restrict__ x, int N, in
   }
 }
 
-cudaError_t launch_transpose_x(const float* x, int n, int D, float* xt, int ld, cudaStream_t st) {
-  if ((D & 3) == 0 && (reinterpret_cast<uintptr_t>(x) & 15u) == 0 && (ld & 3) == 0)
+// Whether transpose_x_kernel (and with it the row maxima) serves x.
+bool transpose_vec(const float* x, int D, int ld) {
+  return (D & 3) == 0 && (reinterpret_cast<uintptr_t>(x) & 15u) == 0 && (ld & 3) == 0;
+}
+cudaError_t launch_transpose_x(const float* x, int n, int D, float* xt, int ld, cudaStream_t st,
+                               const RowMaxJob& job = RowMaxJob()) {
+  if (transpose_vec(x, D, ld))
     transpose_x_kernel<<<dim3((D + 63) / 64, (unsigned)((ld + 63) / 64)), 256, 0, st>>>(x, n, D,
-                                                                                     xt, ld);
+                                                                                     xt, ld, job);
   else
     transpose_x_scalar_kernel<<<dim3((D + 31) / 32, (unsigned)((ld + 31) / 32)), dim3(32, 8), 0,
                                 st>>>(x, n, D, xt, ld);
@@ -1999,6 +2106,9 @@ void mma_fill_args(void* dst, const MmaPlan& p, const Tables& tb, const Function
   a.gout = nullptr;
   a.d2out = nullptr;
   a.zbuf = nullptr;
+  a.tabt = 0;
+  a.rowpm = nullptr;
+  a.ntx = a.pm_ld = 0;
   if (tf32) set_acc_regions<M_TF32>(a, npad_of(F.max_n));
   else set_acc_regions<M_EXACT>(a, npad_of(F.max_n));
   memcpy(dst, &a, sizeof(a));
@@ -2100,7 +2210,17 @@ cudaError_t launch_split(const MmaPlan& p, const Tables& tb, const Function& F, 
       buf = nullptr;
     }
   };
-  if (use_xt) alloc(off_xt + (size_t)D * ld * sizeof(float));
+  // Scaled-mode members (EXACT, FP16X3) need each row's max_j |x_j - o_j|
+  // before their first stage; the transpose forms it in partials of 64
+  // variables while it reads x, instead of the producers reading the rows
+  // once more.
+  bool scaled = false;
+  for (int gi = 0; gi < sp.ngroups; ++gi)
+    scaled |= sp.mode[gi] == CUROB_PRECISION_EXACT || sp.mode[gi] == CUROB_PRECISION_FP16X3;
+  const int ntx = (D + 63) / 64;
+  const size_t off_pm = off_xt + ((size_t)D * ld * sizeof(float) + 255) / 256 * 256;
+  const size_t pm_bytes = scaled ? (size_t)F.ncomp * ntx * ld * sizeof(float) : 0;
+  if (use_xt) alloc(off_pm + pm_bytes);
   if (!buf) {
     use_xt = false;
     sp = split_plan(F, cmode, N, false);  // every member through the contraction
@@ -2122,12 +2242,32 @@ cudaError_t launch_split(const MmaPlan& p, const Tables& tb, const Function& F, 
     XtView xv;
     CUtensorMap map;
     if (use_xt) {
-      e = launch_transpose_x(xs, n, D, xtp, ld, st);
+      RowMaxJob job;
+      float* pm = reinterpret_cast<float*>(static_cast<char*>(buf) + off_pm);
+      const bool with_pm = scaled && transpose_vec(xs, D, ld);
+      if (with_pm)
+        for (int gi = 0; gi < sp.ngroups; ++gi) {
+          if (sp.mode[gi] != CUROB_PRECISION_EXACT && sp.mode[gi] != CUROB_PRECISION_FP16X3)
+            continue;
+          for (int k = 0; k < sp.nlist[gi]; ++k) {
+            const int c = sp.list[gi][k];
+            // component c's vectors start at (F.comp0 + c) D in the instance
+            job.o[job.nc] = p.onat + (size_t)(F.comp0 + c) * D;
+            job.pm[job.nc] = pm + (size_t)c * ntx * ld;
+            ++job.nc;
+          }
+        }
+      e = launch_transpose_x(xs, n, D, xtp, ld, st, job);
       if (e == cudaSuccess &&
           encode_2d(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, xtp, (uint64_t)n, (uint64_t)D,
                     (uint64_t)ld * sizeof(float), kTileM, 1, CU_TENSOR_MAP_SWIZZLE_NONE)) {
         xv.xt = xtp;
         xv.map = &map;
+      }
+      if (e == cudaSuccess && with_pm) {
+        xv.pm = pm;
+        xv.ntx = ntx;
+        xv.pm_ld = ld;
       }
     }
     if (sp.direct) {
