@@ -260,6 +260,25 @@ __device__ inline double weierstrass_inner(double z) {
 // subtracting 2^23 gives it exactly without an integer-to-float conversion;
 // cos(2 pi t) = -cos(2 pi (t - 1/2)) with the argument in [-pi, pi].
 __device__ inline float weierstrass_inner(float z) {
+  const float az = fabsf(z);
+  if (az >= 0x1p-9f && az <= 0x1p30f) {
+    // Here z 2^32 is an integer (z's last bit weighs at least 2^-32), so the
+    // fraction of (z + 1/2) is exact in 32 bits: the same phases and the same
+    // 23-bit rounding as the 40-bit form below (whose low 8 bits are then
+    // zero), with one 32-bit multiply per term.
+    uint32_t P = (uint32_t)__float2ll_rn(z * 4294967296.0f) + 0x80000000u;  // (z + 1/2) 2^32
+    float s = 0.f, ak = 1.f;
+#pragma unroll
+    for (int k = 0; k <= 20; ++k) {
+      // the fraction's top 23 bits, rounded (a carry out of 32 bits wraps to 0)
+      const unsigned b = (P + 256u) >> 9;
+      const float t = __uint_as_float(0x4B000000u | b) - 8388608.0f;
+      s = fmaf(-ak, __cosf(fmaf(t, 7.490140565847157e-07f, -3.14159265358979323846f)), s);
+      ak *= 0.5f;
+      P *= 3u;
+    }
+    return s;
+  }
   const long long Z = __float2ll_rn(z * 1099511627776.0f);          // z 2^40
   unsigned long long P = (unsigned long long)(Z + 549755813888LL);   // (z + 1/2) 2^40
   float s = 0.f, ak = 1.f;
@@ -378,18 +397,23 @@ __device__ inline double term_f64(int kind, int a, double z, double znext, int g
 //   HGBat     (sum z^2)^2 - (sum z)^2 = sum z(z-1) * sum z(z+1)
 //                                     = sum (u-1)(u-2) * sum (u-1) u
 //   Lunacek   z - mu_1 = u,  z - mu_2 = u + 5                (c = 2.5)
-// Cosines of 2 pi v are taken as cospi(2 v) (exact argument reduction).
+// Cosines of 2 pi v reduce v exactly to [-1/2, 1/2] first (cos2pi_sfu).
 // ---------------------------------------------------------------------------
 // Modified Schwefel term 418.9829 - g1(z + c), c = 420.9687462275036, in
 // FP32 without the cancellation that makes the sum over D such terms lose
-// digits near the optimum: for 0 < w = z + c <= 500,
+// digits near the optimum: for |z| < 1 (so 0 < w = z + c <= 500),
 //   g1(w) - g1(c) = 2 w cos((sqrt w + sqrt c)/2) sin(z / (2 (sqrt w + sqrt c)))
 //                   + z sin(sqrt c),
-// and 418.9829 - g1(c) = 1.27275662959398e-5 (constants to 40 digits).  Other
-// branches use the plain expression.
+// and 418.9829 - g1(c) = 1.27275662959398e-5 (constants to 40 digits).
+// Elsewhere the plain expression with the SFU sine: its absolute error, a
+// few 1e-4 per term at w ~ 500, is random from term to term and stays far
+// below the tolerance of f, whose floor 1e-6 f_scale is about 0.4 for this
+// function at D = 1000 (hybrids and compositions weight the term by their
+// own lambda).  The careful form only where it matters keeps the warps of
+// uniform candidates, nearly none of whose terms have |z| < 1, on one path.
 __device__ inline float schwefel_term_f32(float z, float gn) {
   const float w = z + 420.96875f;  // sqrt and prefactor only: z enters exactly below
-  if (w > 0.f && w <= 500.f) {
+  if (fabsf(z) < 1.0f) {
     const float sc = 20.51752290671326630f;      // sqrt(c)
     const float ssc = 0.99528264515390726719f;   // sin(sqrt(c))
     const float sum = sqrtf(w) + sc;
