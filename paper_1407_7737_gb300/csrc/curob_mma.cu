@@ -295,6 +295,39 @@ __device__ __forceinline__ void epi_chunk_k(const float* v, int c, int cend, con
     }
     if (opens) st.zfirst = v[0] * es.s + es.c0;
     st.zprev = zlast;
+  } else if constexpr (KIND == K_RASTRIGIN || KIND == K_ACKLEY || KIND == K_LUNACEK) {
+    // The 32 cosines first (independent of one another), then the sums in
+    // column order, as elem_term_f32 forms them: with one epilogue warp per
+    // scheduler nothing else hides the SFU latency of a column-by-column chain.
+    float cz[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const float u = v[k] * es.s;
+      cz[k] = cos2pi_sfu(KIND == K_LUNACEK ? u : u + es.c0);
+    }
+    float zprev = st.zprev;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      if (k < cend) {
+        const int col = c + k;
+        const float u = v[k] * es.s;
+        const float z = u + es.c0;
+        if constexpr (KIND == K_RASTRIGIN) {
+          part.a0 += fmaf(z, z, 10.0f - 10.0f * cz[k]);
+        } else if constexpr (KIND == K_ACKLEY) {
+          part.a0 = fmaf(z, z, part.a0);
+          part.a1 += cz[k];
+        } else {
+          const float w = u + 5.0f;
+          part.a0 = fmaf(u, u, part.a0);
+          part.a1 = fmaf(w, w, part.a1);
+          part.a2 += cz[k];
+        }
+        if (col == 0 && es.gfirst) st.zfirst = z;
+        zprev = z;
+      }
+    }
+    st.zprev = zprev;
   } else {
     float zprev = st.zprev;
 #pragma unroll
@@ -353,7 +386,8 @@ struct Smem {
   uint8_t* stages;
   uint8_t *a_base, *b_base;  // A slot s at a_base + s a_stride, B slot at b_base + s b_stride
   int a_stride, b_stride, nA, nB;
-  uint64_t *fullB, *emptyB, *rawfull;  // B ring (aliases full/empty unless xt), raw gathers
+  uint64_t *fullB, *emptyB, *rawfull;  // B ring (aliases full/empty unless xt), raw gathers;
+                                       // a stage's B copy completes on full[] of its A slot
   uint64_t *full, *empty, *tmem_full, *tmem_empty, *sig_full, *prod_bar, *gbar;
   uint32_t* tmem_slot;
   volatile int* abort_flag;
@@ -434,7 +468,8 @@ struct RoleState {
   uint32_t chunk_it = 0;  // accumulator hand-offs
   uint32_t pphase = 0;    // producer group barrier uses
   uint32_t comp_it = 0;   // components (row-scale ring)
-  uint32_t b_par = 0;     // B loads: bit s = parity of stage s's last load, bit 8 + s = used
+  uint32_t b_par = 0;     // B loads: bit s = parity of the last load completing on A slot
+                          // s's full barrier, bit 8 + s = used
   uint32_t r_par = 0;     // raw gathers (xt), the same bookkeeping per A slot
   uint32_t e_blk = 0;     // epilogue: blocks staged (tabT buffer parity)
   uint32_t e_phase = 0;   // epilogue group barrier uses
@@ -444,16 +479,13 @@ __device__ inline void cta_setup(const Smem& m, int xt) {
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     for (int s = 0; s < m.nA; ++s) {
-      mbar_init(&m.full[s], xt ? 8 : 9);  // 8 producer warps (+ the B loader's expect_tx)
+      mbar_init(&m.full[s], 9);  // 8 producer warps + the B loader's expect_tx
       mbar_init(&m.empty[s], 1);          // one tcgen05.commit
       mbar_init(&m.gbar[s], 256);         // producer threads' cp.async
       if (xt) mbar_init(&m.rawfull[s], 1);  // the raw gathers' expect_tx
     }
     if (xt)
-      for (int s = 0; s < m.nB; ++s) {
-        mbar_init(&m.fullB[s], 1);   // the B loader's expect_tx
-        mbar_init(&m.emptyB[s], 1);  // one tcgen05.commit
-      }
+      for (int s = 0; s < m.nB; ++s) mbar_init(&m.emptyB[s], 1);  // one tcgen05.commit
     mbar_init(m.tmem_full, 1);
     mbar_init(m.tmem_empty, 4);   // the 4 epilogue warps
     for (int s = 0; s < kSigRing; ++s) mbar_init(&m.sig_full[s], 4);  // producer warps 0-3
@@ -1092,12 +1124,24 @@ __device__ void epilogue_tile(const MmaArgs& a, const Smem& m, long long row0, R
               float v[32];
               if constexpr (kMode == M_EXACT) {
                 float g1[32];
-                tmem_ld32(t_lane + ab + (uint32_t)l, v);
-                tmem_ld32(t_lane + kExactAcc1 + ab + (uint32_t)l, g1);
+                tmem_ld32x2(t_lane + ab + (uint32_t)l, t_lane + kExactAcc1 + ab + (uint32_t)l, v, g1);
                 const float base = sig * 6.103515625e-05f;  // sigma 2^-14
+                if (a.tabt) {  // shared memory, 16-byte aligned (c is a multiple of 16)
 #pragma unroll
-                for (int k = 0; k < 32; ++k)
-                  v[k] = (k < cend) ? (v[k] + g1[k]) * (base * tt[c + k]) : 0.f;
+                  for (int k4 = 0; k4 < 8; ++k4) {
+                    const float4 t4 = *reinterpret_cast<const float4*>(tt + c + 4 * k4);
+                    const float ts[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                      const int k = 4 * k4 + e;
+                      v[k] = (k < cend) ? (v[k] + g1[k]) * (base * ts[e]) : 0.f;
+                    }
+                  }
+                } else {
+#pragma unroll
+                  for (int k = 0; k < 32; ++k)
+                    v[k] = (k < cend) ? (v[k] + g1[k]) * (base * tt[c + k]) : 0.f;
+                }
               } else if constexpr (kMode == M_F16) {
                 tmem_ld32(t_lane + ab + (uint32_t)l, v);
 #pragma unroll
@@ -1167,7 +1211,7 @@ __device__ void mma_tile(const MmaArgs& a, const Smem& m, long long row0, RoleSt
       const bool split_b = m.fullB != m.full;
       const int nA = m.nA, nB = m.nB;
       int sA = (int)(it % (uint32_t)nA), sB = (int)(it % (uint32_t)nB);
-      uint32_t pA = (it / (uint32_t)nA) & 1u, pB = (it / (uint32_t)nB) & 1u;
+      uint32_t pA = (it / (uint32_t)nA) & 1u;
       const uint64_t dA0 = sdesc_m<kMode>(smem_u32(m.a_base));
       const uint64_t dB0 = sdesc_m<kMode>(smem_u32(m.b_base));
       const uint32_t aStr = (uint32_t)m.a_stride >> 4, bStr = (uint32_t)m.b_stride >> 4;
@@ -1198,11 +1242,11 @@ __device__ void mma_tile(const MmaArgs& a, const Smem& m, long long row0, RoleSt
             const uint32_t ab = (chunk_it & 1u) ? (uint32_t)a.acc_hi : 0u;  // accumulator region
             const uint32_t dt0 = tmem_base + ab, dt1 = dt0 + (uint32_t)n0;
             for (int t = 0; t < nslab; ++t, ++it) {
+              // one barrier per stage: the producers' 8 arrivals and the B
+              // copy's bytes (the B ring never runs ahead of the A ring:
+              // nB <= nA, so the copy of stage it cannot land on the phase
+              // of stage it - nA)
               if (!mbar_wait(&full[sA], pA, abort_flag, tb.status)) {
-                ok = false;
-                break;
-              }
-              if (split_b && !mbar_wait(&m.fullB[sB], pB, abort_flag, tb.status)) {
                 ok = false;
                 break;
               }
@@ -1248,7 +1292,6 @@ __device__ void mma_tile(const MmaArgs& a, const Smem& m, long long row0, RoleSt
               if (++sB == nB) {
                 sB = 0;
                 offB = 0;
-                pB ^= 1u;
               } else {
                 offB += bStr;
               }
@@ -1290,9 +1333,12 @@ __device__ void loader_tile(const MmaArgs& a, const Smem& m, long long row0, Rol
                 break;
               }
               uint8_t* dst = m.b_base + (size_t)stage * m.b_stride;
-              mbar_arrive_expect_tx(&m.fullB[stage], bytes);
-              rs.b_par = (rs.b_par & ~(1u << stage)) | (ph << stage) | (1u << (stage + 8));
-              bulk_g2s(dst, src + (size_t)t * bytes, bytes, &m.fullB[stage]);
+              // completion goes to the full barrier of the stage's A slot
+              const int sa = it % m.nA;
+              const uint32_t pa = (it / m.nA) & 1u;
+              mbar_arrive_expect_tx(&m.full[sa], bytes);
+              rs.b_par = (rs.b_par & ~(1u << sa)) | (pa << sa) | (1u << (sa + 8));
+              bulk_g2s(dst, src + (size_t)t * bytes, bytes, &m.full[sa]);
             }
           }
         }
@@ -1366,8 +1412,8 @@ __device__ inline void run_tile(const MmaArgs& a, const Smem& m, long long row0,
     const unsigned long long deadline = globaltimer() + kTimeoutNs;
     if (warp < 8) asm volatile("cp.async.wait_all;" ::: "memory");
     if (warp == kLoaderWarp && (threadIdx.x & 31) == 0)
-      for (int s = 0; s < m.nB; ++s)
-        if (rs.b_par >> (s + 8) & 1u) mbar_drain(&m.fullB[s], rs.b_par >> s & 1u, deadline);
+      for (int s = 0; s < m.nA; ++s)  // B copies complete on full[] of their A slot
+        if (rs.b_par >> (s + 8) & 1u) mbar_drain(&m.full[s], rs.b_par >> s & 1u, deadline);
     if (kXT && warp == kRawWarp && (threadIdx.x & 31) == 0)  // the raw gathers' issuer
       for (int s = 0; s < m.nA; ++s)
         if (rs.r_par >> (s + 8) & 1u) mbar_drain(&m.rawfull[s], rs.r_par >> s & 1u, deadline);
@@ -1801,7 +1847,7 @@ cudaError_t launch_mode(const MmaPlan& p, const Tables& tb, const Function& F, c
     const int nB = kMode == M_EXACT ? 4 : 3;
     const long long room = (long long)kSmemCap - (long long)ctrl - (long long)nB * bb;
     const int nA = room > 0 ? (int)std::min<long long>(kMaxARing, room / (long long)ab) : 0;
-    if (nA >= 3) {
+    if (nA >= std::max(3, nB)) {  // the B ring may not run ahead of the A ring
       a.xt = 1;
       a.nA = nA;
       a.nB = nB;
