@@ -1844,9 +1844,15 @@ cudaError_t launch_mode(const MmaPlan& p, const Tables& tb, const Function& F, c
     // the candidates' operands with their raw gathers inside
     const size_t ab = (size_t)C::kParts * C::kPart;
     const size_t bb = (size_t)C::kParts * ncmax * C::kRow;
-    const int nB = kMode == M_EXACT ? 4 : 3;
-    const long long room = (long long)kSmemCap - (long long)ctrl - (long long)nB * bb;
-    const int nA = room > 0 ? (int)std::min<long long>(kMaxARing, room / (long long)ab) : 0;
+    auto a_slots = [&](int nb) {
+      const long long room = (long long)kSmemCap - (long long)ctrl - (long long)nb * bb;
+      return room > 0 ? (int)std::min<long long>(kMaxARing, room / (long long)ab) : 0;
+    };
+    int nB = kMode == M_EXACT ? 4 : 3;
+    int nA = a_slots(nB);
+    // blocks wider than 352 (hybrids' 400-variable blocks at D = 1000): two B
+    // slots, so that three A slots still fit beside them
+    if (nA < 3 && kMode != M_EXACT) nA = a_slots(nB = 2);
     if (nA >= std::max(3, nB)) {  // the B ring may not run ahead of the A ring
       a.xt = 1;
       a.nA = nA;
