@@ -122,10 +122,14 @@ curob_status curob_evaluate(int fid, const double* x, int N, double* out, curob_
  * in the precision set by curob_set_precision, reductions are carried in
  * FP64 across lanes.  A function with a block of a heavy kind (see
  * curob_query_launches), or a MIXED composition, takes a second kernel on
- * the same stream, with scratch (4 bytes per heavy variable and 80 bytes
- * per candidate, at most 256 MB, candidates in slices beyond that) taken
- * stream-ordered from a pool the library keeps; calls on different streams
- * may run concurrently.  If that scratch cannot be had, a function with one
+ * the same stream.  Scratch, taken stream-ordered from a pool the library
+ * keeps, per slice of candidates (the heavy-kind part at most 256 MB,
+ * candidates in slices beyond that): the transposed copy of the slice's x
+ * (4 D bytes per candidate), 4 bytes per heavy variable and 80 bytes per
+ * candidate for the second kernel, and, when a member runs on EXACT or
+ * FP16X3, 4 bytes per candidate and 64 variables of each component for the
+ * row maxima those precisions scale by; calls on different streams may run
+ * concurrently.  If that scratch cannot be had, a function with one
  * precision group falls back to the single fused launch, and a MIXED
  * composition returns CUDA.  Same errors as curob_evaluate, plus
  * UNSUPPORTED if a forced precision cannot handle the instance's block
